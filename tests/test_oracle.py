@@ -1,0 +1,282 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+Each test states the passage or identity it pins.  None of them re-derives the
+oracle's own formula: the checks are hand values, library routines (numpy /
+scipy), brute force on tiny inputs, closed forms and invariances.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.stats
+
+import oracle
+from paper_2510_18136_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rows(name):
+    out = []
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                out.append(line.split())
+    return out
+
+
+# ----------------------------------------------------------------------------- delay table
+
+def test_delay_table_hand_values():
+    """Sec. 2.2 delay law; hand-computed delays (tests/golden/delays.txt)."""
+    freq = synth.band_centres()
+    for dm, ts, k, _delay, shift in _rows("delays.txt"):
+        tab = oracle.delay_table(freq, [float(dm)], 4.149, float(ts))
+        assert tab[0, int(k)] == int(shift), (dm, k)
+
+
+def test_delay_table_zero_dm_and_top_subband():
+    """DM 0 has no delay; the top subband is the reference frame (delay 0)."""
+    freq = synth.band_centres()
+    tab = oracle.delay_table(freq, np.linspace(0, 4000, 97))
+    assert (tab[0] == 0).all()
+    assert (tab[:, -1] == 0).all()
+    # delays grow with DM and towards low frequency
+    assert (np.diff(tab, axis=0) >= 0).all()
+    assert (np.diff(tab, axis=1) <= 0).all()
+
+
+def test_delay_table_pulsar_at_dm0_trial():
+    """Sec. 3.3: B0329+54 (DM 26.76) is detected at the DM = 0 trial at 134 ms."""
+    freq = synth.band_centres()
+    tab = oracle.delay_table(freq, [0.0, 26.7641])
+    assert (tab[1] == tab[0]).all()
+
+
+def test_delay_table_longest_timescale_single_sample():
+    """Sec. 2.2: at 10.05 s sampling the delay of DM < ~20000 spans at most one sample."""
+    freq = synth.band_centres()
+    tab = oracle.delay_table(freq, np.linspace(0, 20000, 41), t_samp_ms=10050.0)
+    assert tab.max() <= 1
+
+
+def test_delay_table_scaled_grid_reuses_shifts():
+    """Sec. 2.2 footnote: 5x the DM range at 5x coarser sampling reuses the same shifts."""
+    freq = synth.band_centres()
+    dms = np.linspace(0, 4000, 16)
+    a = oracle.delay_table(freq, dms, t_samp_ms=134.2)
+    b = oracle.delay_table(freq, 5.0 * dms, t_samp_ms=5 * 134.2)
+    assert (a == b).all()
+
+
+def test_delay_table_unique_rows_of_grids():
+    """Counts of distinct shift rows of the 64- and 256-trial grids (hand-checked: 40, 101)."""
+    freq = synth.band_centres()
+    t64 = oracle.delay_table(freq, np.linspace(0, 2000, 64))
+    t256 = oracle.delay_table(freq, np.linspace(0, 4000, 256))
+    assert len({r.tobytes() for r in t64}) == 40
+    assert len({r.tobytes() for r in t256}) == 101
+    assert t64.max() == 8 and t256.max() == 16
+
+
+# ----------------------------------------------------------------------------- de-dispersion / boxcar
+
+def _rand_cube(rng, n, n_sub, n_t):
+    return rng.standard_normal((n, n_sub, n_t)).astype(np.float32)
+
+
+def test_dm0_is_plain_subband_sum_and_boxcar_is_convolution():
+    """DM = 0 de-dispersion is the plain subband sum; boxcars are np.convolve 'valid'."""
+    rng = np.random.default_rng(1)
+    x = _rand_cube(rng, 5, 16, 300)
+    widths = [1, 2, 3, 7, 16, 64, 300]
+    res = oracle.search(x, 4.0, np.zeros((1, 16), np.int32), widths)
+    ts = x.astype(np.float64).sum(axis=1)
+    for p in range(5):
+        for wi, w in enumerate(widths):
+            conv = np.convolve(ts[p], np.ones(w), mode="valid") / (4.0 * math.sqrt(w))
+            assert res["snr"][p, 0, wi] == pytest.approx(conv.max(), rel=1e-12, abs=1e-12)
+            assert res["tidx"][p, 0, wi] == int(np.argmax(conv))
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_prefix_form_equals_brute_force(seed):
+    """Brute force on tiny cubes: Python enumeration == C direct sums == C prefix sums."""
+    rng = np.random.default_rng(seed)
+    n, n_sub, n_t = 3, 4, 23
+    x = _rand_cube(rng, n, n_sub, n_t)
+    shifts = np.array([[0, 0, 0, 0], [3, 2, 1, 0], [7, 4, 2, 0], [22, 1, 0, 0],
+                       [30, 0, 0, 0]], np.int32)
+    widths = [1, 2, 5, 8, 23]
+    sig = rng.uniform(0.5, 2.0, size=n)
+    ref_snr, ref_t = oracle.brute_force_search(x, sig, shifts, widths)
+    for direct in (True, False):
+        res = oracle.search(x, sig, shifts, widths, direct=direct)
+        fin = np.isfinite(ref_snr)
+        assert (np.isfinite(res["snr"]) == fin).all()
+        np.testing.assert_allclose(res["snr"][fin], ref_snr[fin], rtol=1e-12, atol=1e-12)
+        assert (res["tidx"] == ref_t).all()
+
+
+def test_no_trials_when_width_exceeds_window():
+    """A (DM, width) pair with w > n_t - smax has no trials: -inf and index -1."""
+    x = np.ones((1, 2, 10), np.float32)
+    res = oracle.search(x, 1.0, np.array([[4, 0]], np.int32), [6, 7])
+    assert res["snr"][0, 0, 0] == pytest.approx(2 * 6 / math.sqrt(6))
+    assert res["snr"][0, 0, 1] == -np.inf and res["tidx"][0, 0, 1] == -1
+
+
+# ----------------------------------------------------------------------------- closed forms
+
+def test_closed_form_small_cube_injection():
+    """North-star closed form A sqrt(w)/sigma per subband (tests/golden/closed_form.txt)."""
+    cfg = synth.config_small()
+    row, col, dmi, wi, ti, snr = _rows("closed_form.txt")[0]
+    tab = oracle.delay_table(cfg.freq_mhz, cfg.dm)
+    inj = oracle.delay_table(cfg.freq_mhz, [500.0])[0]
+    cube = np.zeros((cfg.n_pix, cfg.n_sub, cfg.n_t), np.float32)
+    p = int(row) * cfg.nx + int(col)
+    for k in range(cfg.n_sub):
+        cube[p, k, 10 + inj[k]:12 + inj[k]] += 3.0
+    res, best, _ = oracle.search_cube(cube, tab, cfg.widths, sigma=4.0, pix=[p])
+    assert best["snr"][0] == pytest.approx(float(snr), abs=1e-5)
+    assert (best["dm_idx"][0], best["w_idx"][0], best["t_idx"][0]) == (int(dmi), int(wi), int(ti))
+    cand = oracle.candidates(best, cfg.threshold, pix=[p])
+    assert list(cand["pix"]) == [p]
+
+
+@pytest.mark.parametrize("w", [1, 3, 16, 100, 1200])
+def test_matched_width_is_the_maximum(w):
+    """Noise-free boxcar at a trial DM: S/N = A n_sub w / (sigma_D sqrt(w)) at the true width."""
+    n_sub, n_t = 16, 1200
+    freq = synth.band_centres()
+    dms = [0.0, 300.0] if w == 1200 else [0.0, 300.0, 1500.0]
+    tab = oracle.delay_table(freq, dms)
+    d = len(dms) - 1 if w < 1200 else 0
+    x = np.zeros((1, n_sub, n_t), np.float32)
+    t0 = 0 if w == 1200 else 17
+    for k in range(n_sub):
+        x[0, k, t0 + tab[d, k]:t0 + tab[d, k] + w] = 0.5
+    widths = sorted({1, 2, 4, 8, 16, 100, 1024, 1200, w})
+    res, best, _ = oracle.search_cube(x, tab, widths, sigma=math.sqrt(n_sub))
+    expect = 0.5 * n_sub * w / (math.sqrt(n_sub) * math.sqrt(w))
+    assert best["snr"][0] == pytest.approx(expect, rel=1e-12)
+    assert widths[best["w_idx"][0]] == w
+    assert best["dm_idx"][0] == d and best["t_idx"][0] == t0
+
+
+def test_noise_snr_is_standard_normal():
+    """Unit-variance noise: S/N at DM 0, width 1 is N(0, 1) (KS test)."""
+    rng = np.random.default_rng(7)
+    x = _rand_cube(rng, 200, 16, 50)
+    res = oracle.search(x, 4.0, np.zeros((1, 16), np.int32), [1])
+    # max over t of 50 samples is not N(0,1); test the S/N series itself via t = argmax set
+    # instead use each pixel's S/N at all t by the DM-0, width-1 identity
+    vals = x.astype(np.float64).sum(axis=1).reshape(-1) / 4.0
+    assert scipy.stats.kstest(vals, "norm").pvalue > 1e-3
+    # the search maximum equals the max of those values per pixel
+    np.testing.assert_allclose(res["snr"][:, 0, 0], vals.reshape(200, 50).max(axis=1), rtol=1e-12)
+
+
+def test_false_alarms_match_gaussian_tail():
+    """Noise only: count of S/N > 3 over independent DM-0, width-1 trials ~ Gaussian tail."""
+    rng = np.random.default_rng(11)
+    x = _rand_cube(rng, 4000, 16, 25)
+    vals = x.astype(np.float64).sum(axis=1) / 4.0
+    expect = vals.size * scipy.stats.norm.sf(3.0)
+    res = oracle.search(x, 4.0, np.zeros((1, 16), np.int32), [1])
+    assert res["snr"].shape == (4000, 1, 1)
+    got = int((vals > 3.0).sum())
+    assert abs(got - expect) < 5 * math.sqrt(expect)
+
+
+# ----------------------------------------------------------------------------- invariances
+
+def test_joint_scaling_and_pixel_permutation_invariance():
+    rng = np.random.default_rng(3)
+    x = _rand_cube(rng, 6, 16, 120)
+    tab = oracle.delay_table(synth.band_centres(), np.linspace(0, 2000, 9))
+    ws = [1, 2, 4, 8, 32, 100]
+    a = oracle.search(x, 4.0, tab, ws)
+    b = oracle.search(x * 2.0, 8.0, tab, ws)
+    np.testing.assert_allclose(a["snr"], b["snr"], rtol=1e-12)
+    perm = rng.permutation(6)
+    c = oracle.search(x[perm], 4.0, tab, ws)
+    np.testing.assert_array_equal(a["snr"][perm], c["snr"])
+
+
+def test_time_shift_moves_toa():
+    tab = oracle.delay_table(synth.band_centres(), [0.0, 1000.0])
+    x = np.zeros((1, 16, 200), np.float32)
+    for k in range(16):
+        x[0, k, 40 + tab[1, k]:44 + tab[1, k]] = 1.0
+    y = np.roll(x, 25, axis=2)
+    _, b1, _ = oracle.search_cube(x, tab, [4], sigma=4.0)
+    _, b2, _ = oracle.search_cube(y, tab, [4], sigma=4.0)
+    assert b2["t_idx"][0] == b1["t_idx"][0] + 25
+    assert b2["snr"][0] == pytest.approx(b1["snr"][0])
+
+
+# ----------------------------------------------------------------------------- tie rules, margin
+
+def test_identical_rows_tie_to_lowest_dm_and_margin_ignores_them():
+    """Identical shift rows tie exactly; the lowest DM index wins and is not a near-tie."""
+    x = np.zeros((1, 2, 30), np.float32)
+    x[0, :, 10] = 5.0
+    shifts = np.array([[1, 0], [0, 0], [0, 0]], np.int32)   # rows 1, 2 identical
+    res, best, _ = oracle.search_cube(x, shifts, [1, 2], sigma=1.0)
+    assert best["dm_idx"][0] == 1 and best["w_idx"][0] == 0 and best["t_idx"][0] == 10
+    # runner-up: width 2 at t = 9 or 10 -> 10/sqrt(2)
+    assert best["margin"][0] == pytest.approx(10.0 - 10.0 / math.sqrt(2.0))
+
+
+def test_serving_window_restriction_is_a_subset():
+    """t_lo restricts trials to t >= t_lo; equals brute force on the restricted range."""
+    rng = np.random.default_rng(5)
+    x = _rand_cube(rng, 2, 4, 40)
+    shifts = np.array([[0, 0, 0, 0], [3, 2, 1, 0]], np.int32)
+    ws = [1, 4, 9]
+    t_lo = np.array([[30, 27, 22], [27, 24, 19]], np.int32)
+    res = oracle.search(x, 2.0, shifts, ws, t_lo=t_lo)
+    for p in range(2):
+        for d in range(2):
+            for wi, w in enumerate(ws):
+                L = 40 - shifts[d].max()
+                vals = [sum(float(x[p, k, u + shifts[d, k]]) for u in range(t, t + w)
+                            for k in range(4)) / (2.0 * math.sqrt(w))
+                        for t in range(t_lo[d, wi], L - w + 1)]
+                assert res["snr"][p, d, wi] == pytest.approx(max(vals), rel=1e-12)
+
+
+# ----------------------------------------------------------------------------- robust normalisation
+
+def test_mad_of_permutation_closed_form():
+    """median(1..1200) = 600.5; |i - 600.5| has 599.5.. twice each, so MAD = (299.5 + 300.5)/2 = 300."""
+    rng = np.random.default_rng(0)
+    v = rng.permutation(np.arange(1, 1201)).astype(np.float64)
+    y, bad = oracle.mad_normalise(v[None, :])
+    assert bad == 0
+    np.testing.assert_allclose(y[0], (v - 600.5) / (1.4826 * 300.0), rtol=1e-14)
+
+
+def test_mad_matches_scipy_and_flags_zero_mad():
+    rng = np.random.default_rng(2)
+    x = rng.standard_t(5, size=(7, 301))
+    y, bad = oracle.mad_normalise(x)
+    med = np.median(x, axis=1, keepdims=True)
+    mad = scipy.stats.median_abs_deviation(x, axis=1)[:, None]
+    np.testing.assert_allclose(y, (x - med) / (1.4826 * mad), rtol=1e-12)
+    spike = np.full((1, 50), 3.0)
+    spike[0, 7] = 100.0
+    _, bad = oracle.mad_normalise(spike)
+    assert bad == 1
+
+
+def test_bf16_rounding_matches_torch():
+    import torch
+    rng = np.random.default_rng(9)
+    a = (rng.standard_normal(10000) * 10).astype(np.float32)
+    ref = torch.from_numpy(a).to(torch.bfloat16).to(torch.float32).numpy()
+    np.testing.assert_array_equal(oracle.bf16_round(a), ref)
