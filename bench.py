@@ -1,0 +1,340 @@
+#!/usr/bin/env python
+"""Benchmark of the image-plane single-pulse search on one or more GB300s.
+
+Workload (per GPU): 301 x 301 pixels, 16 subbands (1311-1498 MHz), 1200
+samples of 134.2 ms, 64 DM trials on 0..2000 pc cm^-3, boxcar widths
+1, 2, 4, ..., 1024 and 1200; PSF-convolved Gaussian noise with 50 injected
+bursts, FP32 storage (--dtype bf16 for 16-bit storage).  One step = one
+nsfrb_search over the whole cube plus the candidate list read back.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle instead, on a bounded pixel sample per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "pixel·DM·width S/N trials/s; % of GB300 HBM peak; p99 block latency (ms)"
+WORKLOAD = "full-window search 301x301 px x 16 sub x 1200 samples, 64 DM 0-2000, 12 widths 1..1024+1200"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--dtype", default="f32", choices=["f32", "bf16"])
+    ap.add_argument("--ny", type=int, default=301)
+    ap.add_argument("--nx", type=int, default=301)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--seed", type=int, default=0)
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "sm_max_mhz": float(d.get("sm_max_mhz", 2070.0)),
+                "source": "measured"}
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "source": "fallback"}
+
+
+# ----------------------------------------------------------------------------- workload
+
+def injection_shifts(native, synth, cfg, dms):
+    """Integer shifts of each injection's own DM, from the library's planner."""
+    order = np.argsort(dms)
+    c = synth.SearchConfig(ny=1, nx=1, n_t=cfg.n_t, freq_mhz=cfg.freq_mhz, dm=np.asarray(dms)[order],
+                           widths=np.array([1], np.int32), t_samp_ms=cfg.t_samp_ms, k_dm_ms=cfg.k_dm_ms)
+    with native.Plan(c) as p:
+        sh = p.delays()
+    out = np.empty_like(sh)
+    out[order] = sh
+    return out
+
+
+def make_cube(native, synth, cfg, seed, device, dtype):
+    import torch
+    cube = synth.psf_noise(cfg, seed, device=device)
+    raw = synth.draw_injections(cfg, 50, seed + 1000, max_width=cfg.n_t)
+    sh = injection_shifts(native, synth, cfg, raw["dm"])
+    inj = synth.place_injections(raw, sh, cfg.n_t, cfg.n_sub, synth.psf_sigma())
+    synth.add_injections(cube, cfg, inj, sh, psf=synth.gaussian_psf())
+    if dtype == "bf16":
+        cube = cube.to(torch.bfloat16)
+    return cube, inj
+
+
+def alg_ops(cfg, plan):
+    """FP32 operations per search launch: for every pixel and distinct shift row u with
+    L = n_t - smax_u samples: (n_sub - 1) L de-dispersion adds, L prefix adds, and for
+    every width 2 (L - w + 1) (boxcar difference and running maximum)."""
+    tab = plan.delays()
+    seen = set()
+    per_pix = 0
+    for d in range(tab.shape[0]):
+        key = tab[d].tobytes()
+        if key in seen:
+            continue
+        seen.add(key)
+        L = cfg.n_t - int(tab[d].max())
+        if L <= 0:
+            continue
+        per_pix += (cfg.n_sub - 1) * L + L
+        for w in cfg.widths:
+            if w <= L:
+                per_pix += 2 * (L - int(w) + 1)
+    return per_pix * cfg.n_pix, len(seen)
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx = max(mx, float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle legs
+
+def oracle_sample_rate(cube_host, cfg, target_s: float, seed: int = 0):
+    """Time the FP64 oracle on a pixel sample sized for about target_s seconds."""
+    import oracle
+    tab = oracle.delay_table(cfg.freq_mhz, cfg.dm, cfg.k_dm_ms, cfg.t_samp_ms)
+    rng = np.random.default_rng(seed)
+    sig = float(cfg.sigma_pix * math.sqrt(cfg.n_sub))
+
+    def run(n):
+        pix = np.sort(rng.choice(cfg.n_pix, size=n, replace=False))
+        x = cube_host[pix].float().numpy()
+        t0 = time.perf_counter()
+        oracle.search_cube(x, tab, cfg.widths, sigma=sig)
+        return time.perf_counter() - t0
+
+    t = run(16)
+    n = int(min(cfg.n_pix, max(16, 16 * target_s / max(t, 1e-3))))
+    t = run(n)
+    trials = n * len(cfg.dm) * len(cfg.widths)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return trials / t, n, t, cores
+
+
+def reference_arm(args):
+    """The oracle as the reference implementation, on the host cores (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_2510_18136_gb300 import synth
+    cfg = synth.config_full_window(args.ny, args.nx)
+    cfg.sigma_pix = synth.psf_sigma()
+    import torch
+    host = synth.psf_noise(cfg, args.seed)          # CPU generation, same recipe
+    per_step = min(20.0, 120.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        oracle_sample_rate(host, cfg, per_step / 4)
+    rates, ns = [], []
+    for k in range(args.steps):
+        r, n, t, cores = oracle_sample_rate(host, cfg, per_step, seed=k)
+        rates.append(r)
+        ns.append(n)
+    value = statistics.median(rates)
+    ms = cfg.n_trials / value * 1e3
+    line = {"metric": METRIC, "value": value, "unit": "trials/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "kind": "FP64 CPU oracle"},
+            "cpu_baseline": {"value": value, "unit": "trials/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{int(np.median(ns))} random pixels per step, all 64 DM x 12 widths"},
+            "e2e": {"value": value, "unit": "trials/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    import torch
+    import torch.distributed as dist
+    from paper_2510_18136_gb300 import native, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+
+    cfg = synth.config_full_window(args.ny, args.nx)
+    cfg.sigma_pix = synth.psf_sigma()
+    cube, inj = make_cube(native, synth, cfg, args.seed + rank, dev, args.dtype)
+    sigma = torch.full((cfg.n_pix,), cfg.sigma_pix * math.sqrt(cfg.n_sub), device=dev)
+    plan = native.Plan(cfg, dtype=args.dtype)
+    stream = torch.cuda.current_stream()
+    ops, n_unique = alg_ops(cfg, plan)
+    elem = 4 if args.dtype == "f32" else 2
+    alg_bytes = cfg.n_pix * cfg.n_sub * cfg.n_t * elem + cfg.n_pix * 4 + cfg.n_pix * 16
+
+    def step():
+        plan.search(cube, sigma, stream=stream)
+        return plan.candidates()
+
+    for _ in range(max(3, args.warmup)):
+        cand = step()
+
+    clocks = ClockSampler(local)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    search_ms = []
+    ev0.record(stream)
+    for _ in range(args.steps):
+        cand = step()
+        search_ms.append(plan.last_timing()[0])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    if world > 1:
+        dist.barrier()
+    ck = clocks.stop()
+    t = torch.tensor([elapsed], device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    elapsed_max = float(t.item())
+    value = world * args.steps * cfg.n_trials / elapsed_max
+
+    # end to end: host cube (pinned) -> device -> search -> candidates back to the host
+    host_cube = cube.cpu().pin_memory()
+    host_sigma = sigma.cpu().pin_memory()
+    plan.search_host(host_cube, host_sigma, stream=stream)
+    plan.candidates()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    n_c = 0
+    for _ in range(args.e2e_steps):
+        plan.search_host(host_cube, host_sigma, stream=stream)
+        n_c = len(plan.candidates())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_s = e0.elapsed_time(e1) / 1e3
+    e2e_t = torch.tensor([e2e_s], device=dev)
+    if world > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = world * args.e2e_steps * cfg.n_trials / float(e2e_t.item())
+
+    pk = peaks()
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    kern_s = statistics.mean(search_ms) / 1e3
+    achieved = ops / kern_s
+    peak_ops = n_sm * 128 * pk["sm_max_mhz"] * 1e6
+    hbm_gbs = alg_bytes / kern_s / 1e9
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "trials/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": elapsed_max / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+        "config": {"workload": WORKLOAD, "ny": cfg.ny, "nx": cfg.nx, "n_sub": cfg.n_sub, "n_t": cfg.n_t,
+                   "n_dm": len(cfg.dm), "n_unique_dm_rows": n_unique, "widths": [int(w) for w in cfg.widths],
+                   "storage": args.dtype, "noise": "known sigma", "l2": "inputs larger than L2 (cube "
+                   f"{alg_bytes / 1e9:.2f} GB)", "parallelism": f"replicas x{world} (pixels of one cube per GPU)"},
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                     "unit": "TFLOP/s", "frac": achieved / peak_ops, "traffic": None,
+                     "kernel": "search_kernel", "kernel_ms": kern_s * 1e3,
+                     "ops_per_launch": ops, "peak_basis": f"{n_sm} SM x 128 FP32 lanes x "
+                     f"{pk['sm_max_mhz']:.0f} MHz ({pk['source']} max clock)"},
+        "hbm": {"achieved_gbs": hbm_gbs, "peak_gbs": pk["hbm_gbs"], "frac": hbm_gbs / pk["hbm_gbs"],
+                "bytes_per_launch": alg_bytes, "peak_source": pk["source"]},
+        "e2e": {"value": e2e_value, "unit": "trials/s", "h2d_bytes_per_step": alg_bytes - cfg.n_pix * 16,
+                "d2h_bytes_per_step": 8 + 24 * n_c},
+        "gpu_launches": 3 * args.steps,
+        "candidates": int(len(cand)), "injections": int(len(inj)),
+        "p99_block_latency_ms": None,
+        "clocks": ck,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r, n, t_cpu, cores = oracle_sample_rate(host_cube, cfg, 12.0)
+        line["cpu_baseline"] = {"value": r, "unit": "trials/s", "cores": cores, "kind": "oracle",
+                                "sample": f"{n} random pixels of the cube, all 64 DM x 12 widths ({t_cpu:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

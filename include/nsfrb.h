@@ -1,0 +1,200 @@
+/*
+ * nsfrb.h -- C ABI of libnsfrb, a GB300 (sm_103a) image-plane single-pulse
+ * search over a cube of dirty images (pixel x subband x time), following the
+ * DSA-110 NSFRB search of arXiv 2510.18136, Sec. 2.2 ("cerberus Search
+ * Pipeline"): per pixel, subbands are shifted by pre-computed integer
+ * dispersion delays and summed for each DM trial, boxcar-filtered over a set
+ * of widths, normalised to S/N by a noise level, maximised over time, and
+ * thresholded (Fig. 1: candidates above the S/N threshold).
+ *
+ * Conventions shared by every call
+ * ---------------------------------
+ * - Every call returns an nsfrb_status.  No call aborts, traps or prints.
+ *   The first CUDA error seen by a plan is latched and returned again by the
+ *   next call on that plan (NSFRB_ECUDA); nsfrb_last_error() gives the text.
+ * - Pointers named d_* are device pointers (cudaMalloc / torch tensors on
+ *   the current device); pointers named h_* are host pointers.  The caller
+ *   owns every buffer it passes.  Arrays inside nsfrb_config are copied by
+ *   nsfrb_plan; they need not outlive the call.
+ * - A plan owns its delay tables, device workspace and streams; it is not
+ *   thread-safe.  Different plans may be used from different threads.
+ * - "stream" arguments are a cudaStream_t passed as void* (0 = legacy
+ *   default stream).
+ *
+ * Notation: pixel p = row * nx + col; subband k (increasing frequency);
+ * sample t; DM trial d; width index w_idx into widths[]; T = n_t.
+ */
+#ifndef NSFRB_H
+#define NSFRB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nsfrb_plan_s *nsfrb_plan_t;
+
+typedef enum {
+    NSFRB_OK = 0,
+    NSFRB_EINVAL = 1,    /* invalid argument or configuration, or zero MAD */
+    NSFRB_ENOMEM = 2,    /* device or host allocation failed / over budget */
+    NSFRB_ECUDA = 3,     /* a CUDA call failed (text: nsfrb_last_error)    */
+    NSFRB_ETIMEOUT = 4,  /* a bounded wait ran out                         */
+    NSFRB_ETRUNC = 5,    /* more results than the caller's capacity        */
+    NSFRB_ENOTREADY = 6  /* no result yet (search not run / block pending) */
+} nsfrb_status;
+
+/* Storage type of the input cube.  Arithmetic is always FP32. */
+enum { NSFRB_F32 = 0, NSFRB_BF16 = 1, NSFRB_F16 = 2 };
+
+/* Noise model (Sec. 2.2: "median subtracted in each pixel ... normalized by
+ * the running standard deviation").
+ * KNOWN: the caller supplies sigma_D(p), the noise of the de-dispersed
+ *        series of pixel p (d_sigma), or NULL for sqrt(n_sub) (unit noise
+ *        per subband); no median subtraction.
+ * MAD:   per (pixel, subband) over the window: x <- (x - median) /
+ *        (1.4826 * MAD), then sigma_D = sqrt(n_sub); d_sigma must be NULL. */
+enum { NSFRB_NOISE_KNOWN = 0, NSFRB_NOISE_MAD = 1 };
+
+/* Output mode.  CANDIDATES: per-pixel maximum + candidate list.  FULL: also
+ * S/N and TOA for every (pixel, DM, width) (Sec. 2.3: S/N and TOA arrays for
+ * all pixels, widths and DM trials are saved). */
+enum { NSFRB_OUT_CANDIDATES = 0, NSFRB_OUT_FULL = 1 };
+
+typedef struct {
+    int32_t ny, nx;          /* image rows, columns (>= 1)                     */
+    int32_t n_sub;           /* subbands, 1..32                                */
+    int32_t n_t;             /* window length in samples, 1..1247              */
+    double t_samp_ms;        /* sampling time, e.g. 134.2                      */
+    double k_dm_ms;          /* dispersion constant in ms GHz^2, e.g. 4.149    */
+    const double *freq_mhz;  /* [n_sub] subband centres, strictly increasing   */
+    int32_t n_dm;            /* DM trials, 1..4096                             */
+    const double *dm;        /* [n_dm] pc cm^-3, nondecreasing, >= 0           */
+    int32_t n_w;             /* widths, 1..16                                  */
+    const int32_t *widths;   /* [n_w] samples, strictly increasing, 1..n_t     */
+    float threshold;         /* candidate iff S/N > threshold (strict)         */
+    int32_t dtype;           /* NSFRB_F32 / NSFRB_BF16 / NSFRB_F16             */
+    int32_t noise_mode;      /* NSFRB_NOISE_KNOWN / NSFRB_NOISE_MAD            */
+    int32_t out_mode;        /* NSFRB_OUT_CANDIDATES / NSFRB_OUT_FULL          */
+    float rescore_eps;       /* BF16/F16 only: pixels whose best S/N lies within
+                                +-rescore_eps of the threshold are searched
+                                again from the FP32 cube when one is given;
+                                <= 0 disables re-scoring                        */
+} nsfrb_config;
+
+/* One candidate: the pixel's best trial (maximum S/N over DM, width, time;
+ * ties go to the smallest DM index, then width index, then time). */
+typedef struct {
+    int32_t row, col;   /* pixel                                               */
+    int32_t dm_idx;     /* index into cfg.dm                                   */
+    int32_t w_idx;      /* index into cfg.widths                               */
+    int32_t t_idx;      /* boxcar start sample in the top-subband frame; the
+                           pulse reaches subband k at t_idx + shift[dm_idx][k] */
+    float snr;
+} nsfrb_candidate;
+
+/* Create a plan (host work only; device memory is allocated on first use).
+ * Computes the integer delay table of Sec. 2.2,
+ *   shift[d][k] = floor(k_dm_ms * dm[d] * (f_k^-2 - f_top^-2) / t_samp_ms + 0.5)
+ * (f in GHz, f_top = highest subband centre), and merges DM trials with
+ * identical shift rows (they produce identical S/N; results keep the lowest
+ * DM index).  Errors: EINVAL (bad config), ENOMEM. */
+nsfrb_status nsfrb_plan(const nsfrb_config *cfg, nsfrb_plan_t *out);
+
+/* Copy the delay table to h_shifts[n_dm * n_sub] (row-major [d][k]). */
+nsfrb_status nsfrb_plan_delays(nsfrb_plan_t plan, int32_t *h_shifts);
+
+/* Number of distinct shift rows and the largest shift of each DM trial
+ * (h_smax[n_dm], or NULL). */
+nsfrb_status nsfrb_plan_info(nsfrb_plan_t plan, int32_t *n_unique, int32_t *h_smax);
+
+/* Search one cube (Sec. 2.2), asynchronously on `stream`.
+ * d_cube:     [ny*nx][n_sub][n_t] in cfg.dtype, pixel-major, contiguous.
+ * d_sigma:    [ny*nx] FP32 sigma_D per pixel (KNOWN mode) or NULL.
+ * d_cube_f32: optional FP32 copy of the cube for re-scoring (BF16/F16 only),
+ *             or NULL.
+ * The valid trials of DM d and width w are t in [0, n_t - smax_d - w]; a pair
+ * with none is skipped (FULL: S/N -inf, t_idx -1).  The caller must keep the
+ * inputs alive and unmodified until the stream reaches the search.
+ * Errors: EINVAL, ENOMEM, ECUDA.  In-kernel conditions (zero MAD) are
+ * reported by nsfrb_candidates. */
+nsfrb_status nsfrb_search(nsfrb_plan_t plan, const void *d_cube, const float *d_sigma,
+                          const void *d_cube_f32, void *stream);
+
+/* Same search from HOST buffers: h_cube (pinned for full speed) is copied to
+ * the device in pixel slabs on a copy stream, overlapped with the search of
+ * the previous slab; h_sigma as d_sigma.  Returns when the search is queued. */
+nsfrb_status nsfrb_search_host(nsfrb_plan_t plan, const void *h_cube, const float *h_sigma,
+                               void *stream);
+
+/* Wait for the last search of this plan and copy its candidates (S/N strictly
+ * above the threshold, ordered by pixel index) to h_out[0..cap).  *n_total is
+ * always set to the full count.  Errors: ENOTREADY (no search yet), ETRUNC
+ * (n_total > cap; the first cap are written), EINVAL (a zero MAD row was
+ * met in MAD mode), ECUDA. */
+nsfrb_status nsfrb_candidates(nsfrb_plan_t plan, nsfrb_candidate *h_out, int32_t cap,
+                              int32_t *n_total);
+
+/* Per-pixel best of the last search: out_snr[ny*nx], out_idx[ny*nx][3] =
+ * (dm_idx, w_idx, t_idx), host or device pointers (either may be NULL).
+ * A pixel with no valid trial has S/N -inf and indices -1.  Waits. */
+nsfrb_status nsfrb_best(nsfrb_plan_t plan, float *out_snr, int32_t *out_idx);
+
+/* FULL mode: S/N [ny*nx][n_dm][n_w] and t_idx (same shape) of the last
+ * search, host or device pointers.  Waits.  EINVAL if out_mode != FULL. */
+nsfrb_status nsfrb_full(nsfrb_plan_t plan, float *out_snr, int16_t *out_t_idx);
+
+/* Device time of the last search: *search_ms covers the search kernel
+ * launch(es) of the last nsfrb_search / nsfrb_search_host (including the
+ * re-score pass), *total_ms the whole queued work up to the candidate list
+ * (either may be NULL).  Measured with CUDA events on the launching stream;
+ * waits for the search.  ENOTREADY before the first search. */
+nsfrb_status nsfrb_last_timing(nsfrb_plan_t plan, float *search_ms, float *total_ms);
+
+/* ---- serving (Sec. 2.2: real-time search of 25-sample blocks arriving every
+ * 3.35 s, with a 3.35 s timeout for missing subband images) ---------------
+ * A plan opened for streaming keeps a rolling on-device window of the last
+ * n_t samples (cfg.dtype storage).  Each pushed block holds n_blk samples in
+ * imager order [n_blk][n_sub][ny][nx] FP32 on the host; it is copied and
+ * transposed into the window, and only the trials that end inside the new
+ * block are searched (t + w - 1 + smax_d >= n_t - n_blk).  The per-block
+ * search runs as a captured CUDA graph.  Subbands missing from
+ * present_mask are zero-filled for that block. */
+
+/* Admit a stream: allocates the window and block buffers if the device has
+ * hbm_budget bytes free beyond what this stream needs (ENOMEM otherwise).
+ * n_blk: samples per block (1..n_t). */
+nsfrb_status nsfrb_stream_open(nsfrb_plan_t plan, int32_t n_blk, size_t hbm_reserve);
+
+/* Bytes of device memory a stream of this plan needs. */
+nsfrb_status nsfrb_stream_bytes(nsfrb_plan_t plan, int32_t n_blk, size_t *bytes);
+
+/* Queue one block (asynchronous; h_block must stay valid until the next
+ * nsfrb_stream_poll returns).  ENOTREADY if the previous block has not been
+ * polled yet. */
+nsfrb_status nsfrb_stream_push(nsfrb_plan_t plan, const float *h_block, uint32_t present_mask);
+
+/* Wait up to timeout_ms for the last pushed block and copy its candidates
+ * (as nsfrb_candidates; t_idx refers to the current window).  ETIMEOUT if it
+ * is not done in time (it stays queued: poll again).  *latency_ms (or NULL)
+ * receives push -> completion device time. */
+nsfrb_status nsfrb_stream_poll(nsfrb_plan_t plan, int32_t timeout_ms, nsfrb_candidate *h_out,
+                               int32_t cap, int32_t *n_total, float *latency_ms);
+
+/* Number of blocks pushed so far (windows before n_t / n_blk blocks are
+ * partly empty: their missing samples are zero). */
+nsfrb_status nsfrb_stream_blocks(nsfrb_plan_t plan, int64_t *n_blocks);
+
+/* Release everything the plan owns (device memory, streams, graphs). */
+void nsfrb_destroy(nsfrb_plan_t plan);
+
+/* Static text for a status, and the last error text recorded on this thread. */
+const char *nsfrb_strerror(nsfrb_status s);
+const char *nsfrb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NSFRB_H */

@@ -1,0 +1,137 @@
+// Internal declarations shared by the host planner and the CUDA kernels of
+// libnsfrb.  Not part of the public C ABI (see include/nsfrb.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace nsfrb {
+
+constexpr int kWarps = 8;                 // warps per search CTA
+constexpr int kThreads = kWarps * 32;     // threads per search CTA
+constexpr int kMaxW = 16;                 // widths per plan
+constexpr int kMaxSub = 32;               // subbands per plan
+constexpr int kMaxT = 1247;               // longest window (32 lanes x 39 samples - 1)
+constexpr int kSmallMax = 16;             // widths <= min(C, 16) use the in-lane path
+constexpr int kHistBins = 256;            // radix-select digit bins (MAD mode)
+
+// Width classes of the boxcar stage.
+enum : int32_t { WC_SMALL = 0, WC_LARGE = 1, WC_GENERIC = 2 };
+
+// Per-pixel best trial (written by the search kernel, read by compaction).
+struct PixRec {
+    float snr;
+    int32_t dm_idx, w_idx, t_idx;
+};
+
+// Same layout as nsfrb_candidate in the public header.
+struct CandRec {
+    int32_t row, col, dm_idx, w_idx, t_idx;
+    float snr;
+};
+
+// Error bits latched by kernels into a device word.
+enum : int32_t { ERR_ZERO_MAD = 1, ERR_WAIT_TIMEOUT = 2 };
+
+// Per-unique-row info words (u_info[u * kInfo + ...]).
+enum { UI_SMAX = 0, UI_FIRST_D = 1, UI_N_D = 2, UI_DOFF = 3, UI_ND = 4, kInfo = 5 };
+
+struct SearchParams {
+    // ---- input cube: element (pixel p, subband k, sample t) lives at
+    //      cube[((p - cube_pix0) * n_sub + k) * row_len + t_off + t]
+    const void *cube;
+    int64_t row_len;       // elements per (pixel, subband) row in memory
+    int64_t cube_pix0;     // pixel index of the cube pointer's first pixel
+    int32_t t_off;         // first window sample inside a row
+    const int32_t *t_off_dev;   // if set, t_off is read from device memory
+    int32_t dtype;         // NSFRB_F32 / BF16 / F16
+    int32_t n_sub, n_t;
+    int32_t Tp;            // shared-memory row pitch (floats)
+    int32_t stage;         // 0 plain loads, 1 bulk FP32 direct, 2 bulk 16-bit staging
+    int32_t stg_pitch;     // staging row pitch in bytes (stage 2); fits any t_off % 8
+    // ---- work items: item i -> pixel (pix_list ? pix_list[i] : pix0 + i)
+    int64_t n_items;
+    int64_t pix0;
+    const int32_t *pix_list;
+    const int32_t *n_items_dev;   // if set, the item count is read from here
+    // ---- noise
+    const float *sigma;    // per absolute pixel, or nullptr
+    float sigma_default;
+    int32_t noise_mode;
+    // ---- delay tables (device memory; copied to shared memory per CTA)
+    int32_t n_u, n_u_active;
+    const int32_t *table;  // [n_u*kInfo info][deltas][n_u*n_sub shifts as int32]
+    int32_t n_deltas;
+    // ---- widths
+    int32_t n_w;
+    int32_t widths[kMaxW];
+    int32_t wclass[kMaxW];
+    int32_t n_small, n_large;   // widths of the in-lane and lane-strided classes
+    int32_t n_dm;
+    int32_t new_blk;       // > 0: only trials that end in the last new_blk samples
+    // ---- outputs (indexed by absolute pixel)
+    PixRec *rec;
+    float *full_snr;       // [pix][n_dm][n_w] or nullptr
+    int16_t *full_t;
+    int32_t *err;
+};
+
+// Shared-memory carve-up, identical on host and device.
+struct SmemLayout {
+    size_t table, xs, stg, pbuf, hist, wbest, sinv, bar, total;
+};
+
+__host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+__host__ __device__ inline SmemLayout smem_layout(const SearchParams &p, int C) {
+    SmemLayout L{};
+    size_t o = 0;
+    L.table = o;
+    o += align_up(sizeof(int32_t) * ((size_t)p.n_u * kInfo + p.n_deltas + (size_t)p.n_u * p.n_sub), 16);
+    L.xs = o;
+    int nbuf = (p.stage == 1) ? 2 : 1;
+    o += align_up(sizeof(float) * (size_t)nbuf * p.n_sub * p.Tp, 128);
+    L.stg = o;
+    if (p.stage == 2) o += align_up((size_t)2 * p.n_sub * p.stg_pitch, 128);
+    L.pbuf = o;
+    o += sizeof(float) * (size_t)kWarps * 32 * C;
+    L.hist = o;
+    if (p.noise_mode == 1) o += sizeof(uint32_t) * (size_t)kWarps * kHistBins;
+    L.wbest = o;
+    o += sizeof(PixRec) * kWarps;
+    L.sinv = o;
+    o += sizeof(float) * kMaxW + sizeof(int32_t) * 4;
+    o = align_up(o, 8);
+    L.bar = o;
+    o += sizeof(unsigned long long) * 2;
+    L.total = o;
+    return L;
+}
+
+// Chunk sizes (samples per lane) with compiled kernels; odd so that lanes
+// reading consecutive chunks hit distinct shared-memory banks.
+constexpr int kChunks[] = {1, 3, 5, 9, 17, 25, 39};
+constexpr int kNumChunks = 7;
+
+inline int pick_chunk(int n_t) {
+    for (int i = 0; i < kNumChunks; ++i)
+        if (32 * kChunks[i] >= n_t + 1) return kChunks[i];
+    return -1;
+}
+
+// Kernel launchers (one translation unit per chunk size).
+cudaError_t launch_search(int C, const SearchParams &p, int grid, size_t smem, cudaStream_t s);
+cudaError_t prepare_search(int C, size_t smem);
+
+// Compaction of per-pixel records into the candidate list ordered by pixel.
+cudaError_t launch_compact(const PixRec *rec, int64_t n_pix, int32_t nx, float thr,
+                           int32_t *block_counts, int32_t n_blocks, CandRec *out,
+                           int32_t *n_out, cudaStream_t s);
+// Pixels whose S/N lies within +-eps of the threshold -> list (unordered).
+cudaError_t launch_rescore_select(const PixRec *rec, int64_t n_pix, float thr, float eps,
+                                  int32_t *list, int32_t *n_list, cudaStream_t s);
+constexpr int kCompactBlock = 1024;
+
+}  // namespace nsfrb

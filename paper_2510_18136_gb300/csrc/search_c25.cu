@@ -1,0 +1,6 @@
+// Search kernel instantiation for chunks of 25 samples per lane (windows up to 799 samples).
+#include "search_impl.cuh"
+
+namespace nsfrb {
+NSFRB_INSTANTIATE_SEARCH(25)
+}  // namespace nsfrb

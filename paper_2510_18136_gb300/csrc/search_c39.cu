@@ -1,0 +1,6 @@
+// Search kernel instantiation for chunks of 39 samples per lane (windows up to 1247 samples).
+#include "search_impl.cuh"
+
+namespace nsfrb {
+NSFRB_INSTANTIATE_SEARCH(39)
+}  // namespace nsfrb

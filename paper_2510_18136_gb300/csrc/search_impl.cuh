@@ -1,0 +1,718 @@
+// Fused image-plane single-pulse search kernel (arXiv 2510.18136, Sec. 2.2):
+// per pixel, de-disperse every DM trial with integer shifts, boxcar-filter
+// every width with prefix sums, normalise to S/N, maximise over time, width
+// and DM.  Included by one translation unit per chunk size C.
+//
+// Organisation (one CTA of 8 warps per pixel, persistent over pixels):
+//  * The pixel's [n_sub][n_t] tile is staged in shared memory (bulk copies
+//    into a double buffer for FP32, or into a 16-bit staging double buffer
+//    that is widened to FP32), with -inf beyond n_t so that every time series
+//    element that would read past the window is non-finite.
+//  * Distinct shift rows (DM trials with identical integer tables are one
+//    row) are split into 8 contiguous groups, one per warp.  A warp builds
+//    the first row of its group from all subbands and each later row from
+//    the previous one by adding/subtracting only the subbands whose shift
+//    changed (sorted DMs change a few subbands per row).
+//  * Lane j owns samples [j*C, (j+1)*C): de-dispersed values D, then the
+//    in-lane prefix Lp and one warp scan of lane totals give P = sum D.
+//  * Widths w <= min(C,16) are evaluated in-lane from Lp (plus a shuffled
+//    halo from the next lane); widths that are multiples of 32 from P
+//    re-read lane-strided (P[32 i + j]) so that P[t + w] is a register of the
+//    same lane; any other width from P in shared memory.
+//  * Elements beyond the valid range are -inf or NaN and are dropped by
+//    fmaxf, so no per-element bounds test is needed.
+#pragma once
+
+#include <climits>
+#include <cmath>
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "nsfrb_internal.h"
+
+namespace nsfrb {
+namespace dev {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr unsigned long long kWaitNs = 2000000000ull;   // bounded waits: 2 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for a phase of an mbarrier with a time limit; false on timeout.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (global_ns() - t0 > kWaitNs) return false;
+        __nanosleep(128);
+    }
+    return true;
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
+                                         unsigned long long *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ float neg_inf() { return __int_as_float(0xff800000); }
+__device__ __forceinline__ float qnan() { return __int_as_float(0x7fffffff); }
+
+__device__ __forceinline__ float load_elem(const void *base, int64_t i, int dtype) {
+    if (dtype == 0) return static_cast<const float *>(base)[i];
+    const unsigned short u = static_cast<const unsigned short *>(base)[i];
+    if (dtype == 1) return __uint_as_float(static_cast<uint32_t>(u) << 16);
+    return __half2float(__ushort_as_half(u));
+}
+
+__device__ __forceinline__ float widen16(unsigned short u, int dtype) {
+    if (dtype == 1) return __uint_as_float(static_cast<uint32_t>(u) << 16);
+    return __half2float(__ushort_as_half(u));
+}
+
+// ------------------------------------------------------------------ radix select (MAD mode)
+
+__device__ __forceinline__ uint32_t f2key(float f) {
+    const uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float key2f(uint32_t k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+// Exact order statistic of rank `rank` (0-based) of v[0..n) by one warp:
+// four 8-bit radix passes over an order-preserving integer key.
+static __device__ __noinline__ float warp_select(const float *v, int n, int rank, uint32_t *hist) {
+    const int lane = threadIdx.x & 31;
+    uint32_t prefix = 0, pmask = 0;
+#pragma unroll 1
+    for (int shift = 24; shift >= 0; shift -= 8) {
+        for (int i = lane; i < kHistBins; i += 32) hist[i] = 0;
+        __syncwarp();
+        for (int i = lane; i < n; i += 32) {
+            const uint32_t key = f2key(v[i]);
+            if ((key & pmask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1u);
+        }
+        __syncwarp();
+        uint32_t cnt[8];
+        uint32_t s = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            cnt[j] = hist[8 * lane + j];
+            s += cnt[j];
+        }
+        uint32_t incl = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const uint32_t excl = incl - s;
+        const bool mine = (static_cast<uint32_t>(rank) >= excl) && (static_cast<uint32_t>(rank) < incl);
+        const unsigned bal = __ballot_sync(kFull, mine);
+        const int src = __ffs(bal) - 1;
+        int digit = 0;
+        uint32_t before = 0;
+        if (mine) {
+            uint32_t acc = excl;
+            bool done = false;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                if (!done && static_cast<uint32_t>(rank) < acc + cnt[j]) {
+                    digit = 8 * lane + j;
+                    before = acc;
+                    done = true;
+                }
+                acc += cnt[j];
+            }
+        }
+        digit = __shfl_sync(kFull, digit, src);
+        before = __shfl_sync(kFull, before, src);
+        rank -= static_cast<int>(before);
+        prefix |= static_cast<uint32_t>(digit) << shift;
+        pmask |= 255u << shift;
+        __syncwarp();
+    }
+    return key2f(prefix);
+}
+
+// Median of v[0..n): middle order statistic, or the mean of the two middle
+// ones for even n.
+static __device__ __noinline__ float warp_median(const float *v, int n, uint32_t *hist) {
+    const float a = warp_select(v, n, (n - 1) / 2, hist);
+    if (n & 1) return a;
+    const float b = warp_select(v, n, n / 2, hist);
+    return 0.5f * (a + b);
+}
+
+// ------------------------------------------------------------------ boxcar building blocks
+
+// In-lane small width W: B[c] = P[t0+c+W] - P[t0+c] from the in-lane prefix Lp
+// (Lp[c] = sum of this lane's D[0..c)) and the halo H[i] = total + Lp_next[i].
+template <int C, int SH, int W>
+__device__ __forceinline__ float small_max_w(const float (&Lp)[C + 1], const float (&H)[SH + 1]) {
+    float m = neg_inf();
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        float b;
+        if (c + W <= C)
+            b = Lp[c + W] - Lp[c];
+        else
+            b = H[c + W - C] - Lp[c];
+        m = fmaxf(m, b);
+    }
+    return m;
+}
+
+template <int C, int SH, int W>
+__device__ __forceinline__ int small_find_w(const float (&Lp)[C + 1], const float (&H)[SH + 1],
+                                            float inv, float target, int t0) {
+    int found = INT_MAX;
+#pragma unroll
+    for (int c = C - 1; c >= 0; --c) {
+        float b;
+        if (c + W <= C)
+            b = Lp[c + W] - Lp[c];
+        else
+            b = H[c + W - C] - Lp[c];
+        if (b * inv == target) found = t0 + c;
+    }
+    return found;
+}
+
+#define NSFRB_SMALL_CASES(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16)
+
+template <int C, int SH>
+__device__ __forceinline__ float small_max(int w, const float (&Lp)[C + 1], const float (&H)[SH + 1]) {
+    switch (w) {
+#define NSFRB_SC(W)                                                 \
+    case W:                                                         \
+        if constexpr (W <= SH) return small_max_w<C, SH, W>(Lp, H); \
+        break;
+        NSFRB_SMALL_CASES(NSFRB_SC)
+#undef NSFRB_SC
+        default:
+            break;
+    }
+    return neg_inf();
+}
+
+template <int C, int SH>
+__device__ __forceinline__ int small_find(int w, const float (&Lp)[C + 1], const float (&H)[SH + 1],
+                                          float inv, float target, int t0) {
+    switch (w) {
+#define NSFRB_SC(W)                                                                  \
+    case W:                                                                          \
+        if constexpr (W <= SH) return small_find_w<C, SH, W>(Lp, H, inv, target, t0); \
+        break;
+        NSFRB_SMALL_CASES(NSFRB_SC)
+#undef NSFRB_SC
+        default:
+            break;
+    }
+    return INT_MAX;
+}
+
+// Lane-strided width 32*M: Ps[i] = P[32 i + lane]; B = Ps[i+M] - Ps[i].
+template <int C, int M>
+__device__ __forceinline__ float large_max_m(const float (&Ps)[C]) {
+    float m = neg_inf();
+#pragma unroll
+    for (int i = 0; i + M < C; ++i) m = fmaxf(m, Ps[i + M] - Ps[i]);
+    return m;
+}
+
+template <int C, int M>
+__device__ __forceinline__ int large_find_m(const float (&Ps)[C], float inv, float target, int lane) {
+    int found = INT_MAX;
+#pragma unroll
+    for (int i = C - 1 - M; i >= 0; --i)
+        if ((Ps[i + M] - Ps[i]) * inv == target) found = 32 * i + lane;
+    return found;
+}
+
+#define NSFRB_LARGE_CASES(X)                                                                     \
+    X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16) X(17) \
+    X(18) X(19) X(20) X(21) X(22) X(23) X(24) X(25) X(26) X(27) X(28) X(29) X(30) X(31) X(32)   \
+    X(33) X(34) X(35) X(36) X(37) X(38)
+
+template <int C>
+__device__ __forceinline__ float large_max(int m, const float (&Ps)[C]) {
+    switch (m) {
+#define NSFRB_LC(M)                                        \
+    case M:                                                \
+        if constexpr (M < C) return large_max_m<C, M>(Ps); \
+        break;
+        NSFRB_LARGE_CASES(NSFRB_LC)
+#undef NSFRB_LC
+        default:
+            break;
+    }
+    return neg_inf();
+}
+
+template <int C>
+__device__ __forceinline__ int large_find(int m, const float (&Ps)[C], float inv, float target,
+                                          int lane) {
+    switch (m) {
+#define NSFRB_LC(M)                                                          \
+    case M:                                                                  \
+        if constexpr (M < C) return large_find_m<C, M>(Ps, inv, target, lane); \
+        break;
+        NSFRB_LARGE_CASES(NSFRB_LC)
+#undef NSFRB_LC
+        default:
+            break;
+    }
+    return INT_MAX;
+}
+
+// Any width from P in shared memory; trials t in [t_lo, L - w].
+__device__ __forceinline__ float generic_max(const float *Pw, int w, int L, int t_lo, int lane) {
+    float m = neg_inf();
+    for (int t = t_lo + lane; t + w <= L; t += 32) m = fmaxf(m, Pw[t + w] - Pw[t]);
+    return m;
+}
+
+__device__ __forceinline__ int generic_find(const float *Pw, int w, int L, int t_lo, int lane,
+                                            float inv, float target) {
+    for (int t = t_lo + lane; t + w <= L; t += 32)
+        if ((Pw[t + w] - Pw[t]) * inv == target) return t;
+    return INT_MAX;
+}
+
+// In-lane prefix of this lane's chunk: Lp[c] = D[0] + ... + D[c-1]; returns the total.
+template <int C>
+__device__ __forceinline__ float lane_prefix(const float (&D)[C], float (&Lp)[C + 1]) {
+    Lp[0] = 0.0f;
+#pragma unroll
+    for (int c = 0; c < C; ++c) Lp[c + 1] = Lp[c] + D[c];
+    return Lp[C];
+}
+
+// Halo for the in-lane small widths: H[i] = this lane's total + the next
+// lane's Lp[i] (= P at the next chunk's sample i, relative to this chunk).
+template <int C, int SH>
+__device__ __forceinline__ void lane_halo(const float (&Lp)[C + 1], float tot, int lane, float (&H)[SH + 1]) {
+    H[0] = 0.0f;
+#pragma unroll
+    for (int i = 1; i <= SH; ++i) {
+        const float v = __shfl_down_sync(kFull, Lp[i], 1);
+        H[i] = (lane == 31) ? qnan() : tot + v;
+    }
+}
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+
+__device__ __forceinline__ int warp_min(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+
+// ------------------------------------------------------------------ the kernel
+
+template <int C, bool FULL>
+__global__ void __launch_bounds__(kThreads, 1) search_kernel(const __grid_constant__ SearchParams p) {
+    constexpr int SH = (C < kSmallMax) ? C : kSmallMax;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const SmemLayout lay = smem_layout(p, C);
+    int32_t *s_table = reinterpret_cast<int32_t *>(smem + lay.table);
+    float *s_xs = reinterpret_cast<float *>(smem + lay.xs);
+    unsigned char *s_stg = smem + lay.stg;
+    float *s_pbuf = reinterpret_cast<float *>(smem + lay.pbuf);
+    uint32_t *s_hist = reinterpret_cast<uint32_t *>(smem + lay.hist);
+    PixRec *s_wbest = reinterpret_cast<PixRec *>(smem + lay.wbest);
+    float *s_inv = reinterpret_cast<float *>(smem + lay.sinv);
+    int32_t *s_flag = reinterpret_cast<int32_t *>(smem + lay.sinv + sizeof(float) * kMaxW);
+    unsigned long long *s_bar = reinterpret_cast<unsigned long long *>(smem + lay.bar);
+
+    const int tid = threadIdx.x;
+    const int t_off = p.t_off_dev ? *p.t_off_dev : p.t_off;
+    const int stg_off = t_off & 7;   // 16-bit element offset of the window in an aligned staged row
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
+    const int n_sub = p.n_sub, n_t = p.n_t, Tp = p.Tp;
+
+    // ---- tables to shared memory
+    const int table_words = p.n_u * kInfo + p.n_deltas + p.n_u * n_sub;
+    for (int i = tid; i < table_words; i += kThreads) s_table[i] = p.table[i];
+    const int32_t *s_info = s_table;
+    const int32_t *s_delta = s_table + p.n_u * kInfo;
+    const int32_t *s_shift = s_delta + p.n_deltas;
+
+    // ---- -inf beyond the window in every staged row (never overwritten)
+    const int nbuf = (p.stage == 1) ? 2 : 1;
+    for (int b = 0; b < nbuf; ++b)
+        for (int i = tid; i < n_sub * (Tp - n_t); i += kThreads) {
+            const int k = i / (Tp - n_t), t = n_t + i % (Tp - n_t);
+            s_xs[(size_t)b * n_sub * Tp + (size_t)k * Tp + t] = neg_inf();
+        }
+    if (tid == 0) {
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
+        s_flag[0] = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_proxy_async();
+    }
+    __syncthreads();
+
+    int64_t n_items = p.n_items;
+    if (p.n_items_dev) n_items = *p.n_items_dev;
+
+    auto item_pixel = [&](int64_t it) -> int64_t {
+        return p.pix_list ? static_cast<int64_t>(p.pix_list[it]) : p.pix0 + it;
+    };
+    // issue the bulk copies of one pixel into buffer b (thread 0 only)
+    auto issue = [&](int64_t it, int b) {
+        const int64_t pix = item_pixel(it);
+        const int64_t row0 = (pix - p.cube_pix0) * n_sub;
+        if (p.stage == 1) {
+            const float *src = static_cast<const float *>(p.cube);
+            float *dst = s_xs + (size_t)b * n_sub * Tp;
+            mbar_expect_tx(&s_bar[b], static_cast<uint32_t>(n_sub * n_t * 4));
+            for (int k = 0; k < n_sub; ++k)
+                bulk_g2s(dst + (size_t)k * Tp, src + (row0 + k) * p.row_len + t_off,
+                         static_cast<uint32_t>(n_t * 4), &s_bar[b]);
+        } else {
+            const unsigned char *src = static_cast<const unsigned char *>(p.cube);
+            unsigned char *dst = s_stg + (size_t)b * n_sub * p.stg_pitch;
+            const int64_t first = static_cast<int64_t>(t_off - stg_off) * 2;   // 16-byte aligned
+            const uint32_t bytes = static_cast<uint32_t>(align_up((size_t)(stg_off + n_t) * 2, 16));
+            mbar_expect_tx(&s_bar[b], bytes * n_sub);
+            for (int k = 0; k < n_sub; ++k)
+                bulk_g2s(dst + (size_t)k * p.stg_pitch, src + (row0 + k) * p.row_len * 2 + first, bytes,
+                         &s_bar[b]);
+        }
+    };
+
+    const int n_ua = p.n_u_active;
+    const int u_lo = (warp * n_ua) / kWarps;
+    const int u_hi = ((warp + 1) * n_ua) / kWarps;
+    float *Pw = s_pbuf + (size_t)warp * 32 * C;
+    const int t0 = lane * C;
+
+    uint32_t phase[2] = {0u, 0u};
+    if (p.stage != 0 && tid == 0 && blockIdx.x < n_items) issue(blockIdx.x, 0);
+
+    int iter = 0;
+    for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x, ++iter) {
+        const int b = (p.stage == 1) ? (iter & 1) : 0;
+        const int sb = iter & 1;   // staging / barrier buffer of this item
+        const int64_t pix = item_pixel(it);
+        const int64_t nxt = it + gridDim.x;
+        // prefetch the next item into the other buffer (free since the end of the previous item)
+        if (p.stage != 0 && tid == 0 && nxt < n_items) issue(nxt, sb ^ 1);
+
+        float *xs = s_xs + (size_t)b * n_sub * Tp;
+        if (p.stage == 0) {
+            const int64_t row0 = (pix - p.cube_pix0) * n_sub;
+            for (int i = tid; i < n_sub * n_t; i += kThreads) {
+                const int k = i / n_t, t = i - k * n_t;
+                xs[(size_t)k * Tp + t] = load_elem(p.cube, (row0 + k) * p.row_len + t_off + t, p.dtype);
+            }
+        } else {
+            const bool ok = mbar_wait(&s_bar[sb], phase[sb]);
+            phase[sb] ^= 1u;
+            if (!ok) atomicOr(&s_flag[0], ERR_WAIT_TIMEOUT);
+            if (p.stage == 2) {
+                const unsigned short *stg =
+                    reinterpret_cast<const unsigned short *>(s_stg + (size_t)sb * n_sub * p.stg_pitch);
+                const int pitch = p.stg_pitch / 2;
+                for (int i = tid; i < n_sub * n_t; i += kThreads) {
+                    const int k = i / n_t, t = i - k * n_t;
+                    xs[(size_t)k * Tp + t] = widen16(stg[(size_t)k * pitch + stg_off + t], p.dtype);
+                }
+            }
+        }
+        if (tid < p.n_w) {
+            const float sg = (p.sigma && p.noise_mode == 0) ? p.sigma[pix] : p.sigma_default;
+            s_inv[tid] = 1.0f / (sg * sqrtf(static_cast<float>(p.widths[tid])));
+        }
+        __syncthreads();
+        if (s_flag[0] & ERR_WAIT_TIMEOUT) {
+            // a bulk copy did not complete in time: record and stop this CTA
+            if (tid == 0) atomicOr(p.err, ERR_WAIT_TIMEOUT);
+            // wait (bounded) for the copies still in flight before leaving
+            if (tid == 0 && p.stage != 0 && nxt < n_items) mbar_wait(&s_bar[sb ^ 1], phase[sb ^ 1]);
+            return;
+        }
+
+        // ---- robust normalisation per (pixel, subband) row (MAD mode)
+        bool bad_pixel = false;
+        if (p.noise_mode == 1) {
+            uint32_t *hist = s_hist + warp * kHistBins;
+            for (int k = warp; k < n_sub; k += kWarps) {
+                float *row = xs + (size_t)k * Tp;
+                const float med = warp_median(row, n_t, hist);
+                for (int t = lane; t < n_t; t += 32) Pw[t] = fabsf(row[t] - med);
+                __syncwarp();
+                const float mad = warp_median(Pw, n_t, hist);
+                if (mad == 0.0f) {
+                    if (lane == 0) atomicOr(&s_flag[0], ERR_ZERO_MAD);
+                } else {
+                    const float inv = 1.0f / (1.4826f * mad);
+                    for (int t = lane; t < n_t; t += 32) row[t] = (row[t] - med) * inv;
+                }
+                __syncwarp();
+            }
+            __syncthreads();
+            bad_pixel = (s_flag[0] & ERR_ZERO_MAD) != 0;
+        }
+
+        // ---- per-warp search over its rows
+        float bsnr = neg_inf();
+        int bu = -1, bwi = -1, bt = -1;
+        float D[C];
+        if (!bad_pixel) {
+#pragma unroll 1
+            for (int u = u_lo; u < u_hi; ++u) {
+                const int32_t *info = s_info + u * kInfo;
+                if (u == u_lo) {
+#pragma unroll
+                    for (int c = 0; c < C; ++c) D[c] = 0.0f;
+                    const int32_t *sh = s_shift + u * n_sub;
+#pragma unroll 1
+                    for (int k = 0; k < n_sub; ++k) {
+                        const float *xr = xs + (size_t)k * Tp + t0 + sh[k];
+#pragma unroll
+                        for (int c = 0; c < C; ++c) D[c] += xr[c];
+                    }
+                } else {
+                    const int d0 = info[UI_DOFF], nd = info[UI_ND];
+#pragma unroll 1
+                    for (int e = d0; e < d0 + nd; ++e) {
+                        const uint32_t pk = static_cast<uint32_t>(s_delta[e]);
+                        const int k = pk & 63u, so = (pk >> 6) & 0x1fffu, sn = pk >> 19;
+                        const float *xo = xs + (size_t)k * Tp + t0 + so;
+                        const float *xn = xs + (size_t)k * Tp + t0 + sn;
+#pragma unroll
+                        for (int c = 0; c < C; ++c) D[c] = (D[c] + xn[c]) - xo[c];
+                    }
+                }
+                const int L = n_t - info[UI_SMAX];
+
+                // in-lane prefix, warp scan of lane totals, P to shared memory
+                const bool masked = p.new_blk > 0;
+                float ls = neg_inf();
+                int lw = -1;
+                auto consider = [&](int wi, float m) {
+                    const float s = m * s_inv[wi];
+                    if (s > ls || (s == ls && wi < lw)) {
+                        ls = s;
+                        lw = wi;
+                    }
+                };
+                // FULL mode: the S/N of (row u, width wi) reduced over the warp, and its TOA
+                auto write_full = [&](int wi, float s, int t) {
+                    if (lane == 0) {
+                        const int fd = info[UI_FIRST_D], ndm = info[UI_N_D];
+                        for (int d = fd; d < fd + ndm; ++d) {
+                            const int64_t o = (pix * p.n_dm + d) * p.n_w + wi;
+                            p.full_snr[o] = s;
+                            p.full_t[o] = static_cast<int16_t>(t == INT_MAX ? -1 : t);
+                        }
+                    }
+                };
+                {
+                    float Lp[C + 1];
+                    const float tot = lane_prefix<C>(D, Lp);
+                    float inc = tot;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const float y = __shfl_up_sync(kFull, inc, o);
+                        if (lane >= o) inc += y;
+                    }
+                    float carry = __shfl_up_sync(kFull, inc, 1);
+                    if (lane == 0) carry = 0.0f;
+#pragma unroll
+                    for (int c = 0; c < C; ++c) Pw[t0 + c] = carry + Lp[c];
+                    if (!masked && p.n_small > 0) {
+                        // small widths, in-lane
+                        float H[SH + 1];
+                        lane_halo<C, SH>(Lp, tot, lane, H);
+#pragma unroll 1
+                        for (int wi = 0; wi < p.n_w; ++wi) {
+                            if (p.wclass[wi] != WC_SMALL) continue;
+                            const int w = p.widths[wi];
+                            const float m = small_max<C, SH>(w, Lp, H);
+                            consider(wi, m);
+                            if constexpr (FULL) {
+                                const float mw = warp_max(m), sw = mw * s_inv[wi];
+                                int t = INT_MAX;
+                                if (mw != neg_inf()) t = warp_min(small_find<C, SH>(w, Lp, H, s_inv[wi], sw, t0));
+                                write_full(wi, sw, t);
+                            }
+                        }
+                    }
+                }
+                __syncwarp();
+                if (!masked && p.n_large > 0) {
+                    // multiples of 32, lane-strided
+                    float Ps[C];
+#pragma unroll
+                    for (int i = 0; i < C; ++i) Ps[i] = Pw[32 * i + lane];
+#pragma unroll 1
+                    for (int wi = 0; wi < p.n_w; ++wi) {
+                        if (p.wclass[wi] != WC_LARGE) continue;
+                        const int mm = p.widths[wi] >> 5;
+                        const float m = large_max<C>(mm, Ps);
+                        consider(wi, m);
+                        if constexpr (FULL) {
+                            const float mw = warp_max(m), sw = mw * s_inv[wi];
+                            int t = INT_MAX;
+                            if (mw != neg_inf()) t = warp_min(large_find<C>(mm, Ps, s_inv[wi], sw, lane));
+                            write_full(wi, sw, t);
+                        }
+                    }
+                }
+                // everything else from shared memory
+#pragma unroll 1
+                for (int wi = 0; wi < p.n_w; ++wi) {
+                    if (!masked && p.wclass[wi] != WC_GENERIC) continue;
+                    const int w = p.widths[wi];
+                    const int tl = masked ? max(0, L - w - p.new_blk + 1) : 0;
+                    const float m = generic_max(Pw, w, L, tl, lane);
+                    consider(wi, m);
+                    if constexpr (FULL) {
+                        const float mw = warp_max(m), sw = mw * s_inv[wi];
+                        int t = INT_MAX;
+                        if (mw != neg_inf()) t = warp_min(generic_find(Pw, w, L, tl, lane, s_inv[wi], sw));
+                        write_full(wi, sw, t);
+                    }
+                }
+
+                // warp arg-max over (S/N, width index)
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float os = __shfl_xor_sync(kFull, ls, o);
+                    const int ow = __shfl_xor_sync(kFull, lw, o);
+                    if (os > ls || (os == ls && ow < lw && ow >= 0)) {
+                        ls = os;
+                        lw = ow;
+                    }
+                }
+                if (ls > bsnr) {
+                    // earliest sample reaching this S/N, re-evaluated exactly as above
+                    // (the prefix and halo are rebuilt from D: same operations, same values)
+                    const int w = p.widths[lw];
+                    const float inv = s_inv[lw];
+                    int t;
+                    if (masked || p.wclass[lw] == WC_GENERIC) {
+                        const int tl = masked ? max(0, L - w - p.new_blk + 1) : 0;
+                        t = generic_find(Pw, w, L, tl, lane, inv, ls);
+                    } else if (p.wclass[lw] == WC_SMALL) {
+                        float Lp[C + 1];
+                        float H[SH + 1];
+                        const float tot = lane_prefix<C>(D, Lp);
+                        lane_halo<C, SH>(Lp, tot, lane, H);
+                        t = small_find<C, SH>(w, Lp, H, inv, ls, t0);
+                    } else {
+                        float Ps[C];
+#pragma unroll
+                        for (int i = 0; i < C; ++i) Ps[i] = Pw[32 * i + lane];
+                        t = large_find<C>(w >> 5, Ps, inv, ls, lane);
+                    }
+                    t = warp_min(t);
+                    bsnr = ls;
+                    bu = u;
+                    bwi = lw;
+                    bt = t;
+                }
+                __syncwarp();
+            }
+        }
+        // FULL mode: DM rows that have no trial at all
+        if (p.full_snr && warp == 0) {
+            for (int u = bad_pixel ? 0 : n_ua; u < p.n_u; ++u) {
+                const int32_t *info = s_info + u * kInfo;
+                const int fd = info[UI_FIRST_D], ndm = info[UI_N_D];
+                for (int i = lane; i < ndm * p.n_w; i += 32) {
+                    const int64_t o = (pix * p.n_dm + fd) * p.n_w + i;
+                    p.full_snr[o] = neg_inf();
+                    p.full_t[o] = -1;
+                }
+            }
+        }
+        if (lane == 0) s_wbest[warp] = PixRec{bsnr, bu, bwi, bt};
+        __syncthreads();
+        if (tid == 0) {
+            PixRec best{neg_inf(), -1, -1, -1};
+            for (int w = 0; w < kWarps; ++w)
+                if (s_wbest[w].snr > best.snr) best = s_wbest[w];
+            if (best.dm_idx >= 0) best.dm_idx = s_info[best.dm_idx * kInfo + UI_FIRST_D];
+            if (bad_pixel) {
+                best = PixRec{neg_inf(), -1, -1, -1};
+                atomicOr(p.err, ERR_ZERO_MAD);
+                s_flag[0] &= ~ERR_ZERO_MAD;
+            }
+            p.rec[pix] = best;
+        }
+        // all reads of this item's buffers are done before they are refilled
+        fence_proxy_async();
+        __syncthreads();
+    }
+}
+
+}  // namespace dev
+
+#define NSFRB_INSTANTIATE_SEARCH(CC)                                                           \
+    cudaError_t launch_search_c##CC(const SearchParams &p, int grid, size_t smem, cudaStream_t s) { \
+        if (p.full_snr)                                                                        \
+            dev::search_kernel<CC, true><<<grid, kThreads, smem, s>>>(p);                      \
+        else                                                                                   \
+            dev::search_kernel<CC, false><<<grid, kThreads, smem, s>>>(p);                     \
+        return cudaGetLastError();                                                             \
+    }                                                                                          \
+    cudaError_t prepare_search_c##CC(size_t smem) {                                            \
+        cudaError_t e = cudaFuncSetAttribute(dev::search_kernel<CC, false>,                    \
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        if (e != cudaSuccess) return e;                                                        \
+        return cudaFuncSetAttribute(dev::search_kernel<CC, true>,                              \
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);   \
+    }
+
+}  // namespace nsfrb

@@ -1,0 +1,265 @@
+"""Thin ctypes binding of libnsfrb (include/nsfrb.h): argument marshalling only.
+
+Every step of the search runs in the library's CUDA kernels; this module only
+checks tensor shapes/devices, passes pointers and sizes, and converts status
+codes to exceptions.  The function names follow the C ABI; ``Plan`` wraps them.
+If the compiled library is missing this module raises at import: there is no
+fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_double, c_float, c_int16, c_int32, c_int64, c_size_t, c_uint32, c_void_p
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+F32, BF16, F16 = 0, 1, 2
+NOISE_KNOWN, NOISE_MAD = 0, 1
+OUT_CANDIDATES, OUT_FULL = 0, 1
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ETRUNC, ENOTREADY = range(7)
+
+_DTYPES = {"f32": F32, "bf16": BF16, "f16": F16}
+_TORCH = {F32: torch.float32, BF16: torch.bfloat16, F16: torch.float16}
+
+
+class nsfrb_config(ctypes.Structure):
+    _fields_ = [("ny", c_int32), ("nx", c_int32), ("n_sub", c_int32), ("n_t", c_int32),
+                ("t_samp_ms", c_double), ("k_dm_ms", c_double), ("freq_mhz", POINTER(c_double)),
+                ("n_dm", c_int32), ("dm", POINTER(c_double)), ("n_w", c_int32),
+                ("widths", POINTER(c_int32)), ("threshold", c_float), ("dtype", c_int32),
+                ("noise_mode", c_int32), ("out_mode", c_int32), ("rescore_eps", c_float)]
+
+
+class nsfrb_candidate(ctypes.Structure):
+    _fields_ = [("row", c_int32), ("col", c_int32), ("dm_idx", c_int32), ("w_idx", c_int32),
+                ("t_idx", c_int32), ("snr", c_float)]
+
+
+CANDIDATE_DTYPE = np.dtype([("row", "<i4"), ("col", "<i4"), ("dm_idx", "<i4"), ("w_idx", "<i4"),
+                            ("t_idx", "<i4"), ("snr", "<f4")])
+
+
+class NsfrbError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {lib.nsfrb_strerror(status).decode()} "
+                         f"({lib.nsfrb_last_error().decode()})")
+        self.status = status
+
+
+def _load() -> ctypes.CDLL:
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"libnsfrb is not built ({path}); run paper_2510_18136_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    P = c_void_p
+    sig = {
+        "nsfrb_plan": ([POINTER(nsfrb_config), POINTER(c_void_p)], c_int32),
+        "nsfrb_plan_delays": ([P, P], c_int32),
+        "nsfrb_plan_info": ([P, POINTER(c_int32), P], c_int32),
+        "nsfrb_search": ([P, P, P, P, P], c_int32),
+        "nsfrb_search_host": ([P, P, P, P], c_int32),
+        "nsfrb_candidates": ([P, P, c_int32, POINTER(c_int32)], c_int32),
+        "nsfrb_best": ([P, P, P], c_int32),
+        "nsfrb_full": ([P, P, P], c_int32),
+        "nsfrb_last_timing": ([P, POINTER(c_float), POINTER(c_float)], c_int32),
+        "nsfrb_stream_open": ([P, c_int32, c_size_t], c_int32),
+        "nsfrb_stream_bytes": ([P, c_int32, POINTER(c_size_t)], c_int32),
+        "nsfrb_stream_push": ([P, P, c_uint32], c_int32),
+        "nsfrb_stream_poll": ([P, c_int32, P, c_int32, POINTER(c_int32), POINTER(c_float)], c_int32),
+        "nsfrb_stream_blocks": ([P, POINTER(c_int64)], c_int32),
+        "nsfrb_destroy": ([P], None),
+        "nsfrb_strerror": ([c_int32], ctypes.c_char_p),
+        "nsfrb_last_error": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    return L
+
+
+lib = _load()
+LIB_PATH = _build.LIB
+
+
+def _check(status: int, what: str, allow=()):
+    if status != OK and status not in allow:
+        raise NsfrbError(status, what)
+    return status
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream) -> c_void_p | None:
+    if stream is None:
+        return c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return c_void_p(stream.cuda_stream)
+    return c_void_p(int(stream))
+
+
+class Plan:
+    """One search configuration (``nsfrb_plan``) and its device workspace."""
+
+    def __init__(self, cfg, dtype: str = "f32", noise: str = "known", out: str = "candidates",
+                 rescore_eps: float = 0.0):
+        self.cfg = cfg
+        self.dtype = _DTYPES[dtype]
+        self._freq = np.ascontiguousarray(cfg.freq_mhz, dtype=np.float64)
+        self._dm = np.ascontiguousarray(cfg.dm, dtype=np.float64)
+        self._w = np.ascontiguousarray(cfg.widths, dtype=np.int32)
+        c = nsfrb_config()
+        c.ny, c.nx, c.n_sub, c.n_t = cfg.ny, cfg.nx, cfg.n_sub, cfg.n_t
+        c.t_samp_ms, c.k_dm_ms = cfg.t_samp_ms, cfg.k_dm_ms
+        c.freq_mhz = self._freq.ctypes.data_as(POINTER(c_double))
+        c.n_dm = self._dm.size
+        c.dm = self._dm.ctypes.data_as(POINTER(c_double))
+        c.n_w = self._w.size
+        c.widths = self._w.ctypes.data_as(POINTER(c_int32))
+        c.threshold = float(cfg.threshold)
+        c.dtype = self.dtype
+        c.noise_mode = NOISE_MAD if noise == "mad" else NOISE_KNOWN
+        c.out_mode = OUT_FULL if out == "full" else OUT_CANDIDATES
+        c.rescore_eps = float(rescore_eps)
+        self.noise_mode = c.noise_mode
+        self.out_mode = c.out_mode
+        h = c_void_p()
+        _check(lib.nsfrb_plan(ctypes.byref(c), ctypes.byref(h)), "nsfrb_plan")
+        self._h = h
+
+    # ------------------------------------------------------------------ plan info
+    @property
+    def handle(self):
+        return self._h
+
+    def delays(self) -> np.ndarray:
+        out = np.empty((self._dm.size, self.cfg.n_sub), dtype=np.int32)
+        _check(lib.nsfrb_plan_delays(self._h, out.ctypes.data_as(c_void_p)), "nsfrb_plan_delays")
+        return out
+
+    def info(self):
+        n_u = c_int32()
+        smax = np.empty(self._dm.size, dtype=np.int32)
+        _check(lib.nsfrb_plan_info(self._h, ctypes.byref(n_u), smax.ctypes.data_as(c_void_p)),
+               "nsfrb_plan_info")
+        return int(n_u.value), smax
+
+    # ------------------------------------------------------------------ search
+    def _check_cube(self, cube: torch.Tensor, dtype: int, device: str):
+        cfg = self.cfg
+        if tuple(cube.shape) != (cfg.n_pix, cfg.n_sub, cfg.n_t):
+            raise ValueError(f"cube shape {tuple(cube.shape)} != {(cfg.n_pix, cfg.n_sub, cfg.n_t)}")
+        if cube.dtype != _TORCH[dtype]:
+            raise ValueError(f"cube dtype {cube.dtype} != {_TORCH[dtype]}")
+        if not cube.is_contiguous():
+            raise ValueError("cube must be contiguous")
+        if (cube.device.type == "cuda") != (device == "cuda"):
+            raise ValueError(f"cube must be on {device}")
+
+    def search(self, cube: torch.Tensor, sigma: torch.Tensor | None = None,
+               cube_f32: torch.Tensor | None = None, stream=None) -> None:
+        """``nsfrb_search`` on a device cube [n_pix, n_sub, n_t] (asynchronous)."""
+        self._check_cube(cube, self.dtype, "cuda")
+        if sigma is not None:
+            assert sigma.is_cuda and sigma.dtype == torch.float32 and sigma.numel() == self.cfg.n_pix
+            assert sigma.is_contiguous()
+        if cube_f32 is not None:
+            self._check_cube(cube_f32, F32, "cuda")
+        _check(lib.nsfrb_search(self._h, _ptr(cube), _ptr(sigma), _ptr(cube_f32),
+                                _stream_handle(stream)), "nsfrb_search")
+
+    def search_host(self, cube: torch.Tensor, sigma: torch.Tensor | None = None, stream=None) -> None:
+        """``nsfrb_search_host`` on a host cube (pinned for full copy speed)."""
+        self._check_cube(cube, self.dtype, "cpu")
+        if sigma is not None:
+            assert not sigma.is_cuda and sigma.dtype == torch.float32 and sigma.is_contiguous()
+        _check(lib.nsfrb_search_host(self._h, _ptr(cube), _ptr(sigma), _stream_handle(stream)),
+               "nsfrb_search_host")
+
+    def candidates(self, cap: int | None = None) -> np.ndarray:
+        """``nsfrb_candidates``: structured array (row, col, dm_idx, w_idx, t_idx, snr)."""
+        n = c_int32()
+        cap = self.cfg.n_pix if cap is None else int(cap)
+        out = np.zeros(cap, dtype=CANDIDATE_DTYPE)
+        st = lib.nsfrb_candidates(self._h, out.ctypes.data_as(c_void_p), cap, ctypes.byref(n))
+        _check(st, "nsfrb_candidates")
+        return out[: n.value]
+
+    def best(self):
+        """``nsfrb_best``: per-pixel S/N [n_pix] and (dm_idx, w_idx, t_idx) [n_pix, 3]."""
+        snr = np.empty(self.cfg.n_pix, dtype=np.float32)
+        idx = np.empty((self.cfg.n_pix, 3), dtype=np.int32)
+        _check(lib.nsfrb_best(self._h, snr.ctypes.data_as(c_void_p), idx.ctypes.data_as(c_void_p)),
+               "nsfrb_best")
+        return snr, idx
+
+    def full(self):
+        """``nsfrb_full``: S/N and t_idx [n_pix, n_dm, n_w] as numpy arrays."""
+        shape = (self.cfg.n_pix, self._dm.size, self._w.size)
+        snr = np.empty(shape, dtype=np.float32)
+        t = np.empty(shape, dtype=np.int16)
+        _check(lib.nsfrb_full(self._h, snr.ctypes.data_as(c_void_p), t.ctypes.data_as(c_void_p)),
+               "nsfrb_full")
+        return snr, t
+
+    def last_timing(self):
+        """``nsfrb_last_timing``: (search-kernel ms, total queued ms) of the last search."""
+        a, b = c_float(), c_float()
+        _check(lib.nsfrb_last_timing(self._h, ctypes.byref(a), ctypes.byref(b)), "nsfrb_last_timing")
+        return float(a.value), float(b.value)
+
+    # ------------------------------------------------------------------ serving
+    def stream_bytes(self, n_blk: int) -> int:
+        b = c_size_t()
+        _check(lib.nsfrb_stream_bytes(self._h, int(n_blk), ctypes.byref(b)), "nsfrb_stream_bytes")
+        return int(b.value)
+
+    def stream_open(self, n_blk: int, hbm_reserve: int = 0) -> None:
+        _check(lib.nsfrb_stream_open(self._h, int(n_blk), int(hbm_reserve)), "nsfrb_stream_open")
+
+    def stream_push(self, block: torch.Tensor, present_mask: int | None = None) -> None:
+        """Push one block [n_blk, n_sub, ny, nx] FP32 (host memory)."""
+        cfg = self.cfg
+        assert not block.is_cuda and block.dtype == torch.float32 and block.is_contiguous()
+        assert block.shape[1:] == (cfg.n_sub, cfg.ny, cfg.nx)
+        mask = (1 << cfg.n_sub) - 1 if present_mask is None else int(present_mask)
+        _check(lib.nsfrb_stream_push(self._h, _ptr(block), c_uint32(mask)), "nsfrb_stream_push")
+
+    def stream_poll(self, timeout_ms: int = 3350, cap: int | None = None):
+        """Returns (candidates, latency_ms) or raises NsfrbError(ETIMEOUT)."""
+        n = c_int32()
+        lat = c_float()
+        cap = self.cfg.n_pix if cap is None else int(cap)
+        out = np.zeros(cap, dtype=CANDIDATE_DTYPE)
+        _check(lib.nsfrb_stream_poll(self._h, int(timeout_ms), out.ctypes.data_as(c_void_p), cap,
+                                     ctypes.byref(n), ctypes.byref(lat)), "nsfrb_stream_poll")
+        return out[: n.value], float(lat.value)
+
+    def stream_blocks(self) -> int:
+        n = c_int64()
+        _check(lib.nsfrb_stream_blocks(self._h, ctypes.byref(n)), "nsfrb_stream_blocks")
+        return int(n.value)
+
+    # ------------------------------------------------------------------ lifetime
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib.nsfrb_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
