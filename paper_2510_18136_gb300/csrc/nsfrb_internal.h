@@ -19,6 +19,15 @@ constexpr int kHistBins = 256;            // radix-select digit bins (MAD mode)
 
 // Width classes of the boxcar stage.
 enum : int32_t { WC_SMALL = 0, WC_LARGE = 1, WC_GENERIC = 2 };
+constexpr int kPow2 = 11;   // power-of-two widths 1 .. 1024 have compile-time code paths
+
+// Class of the power-of-two width 2^J for chunk size C: in-lane (<= min(C, 16)),
+// lane-strided (32 M with M < C), or shared-memory generic.
+__host__ __device__ constexpr int pow2_class(int C, int J) {
+    return ((1 << J) <= (C < kSmallMax ? C : kSmallMax))
+               ? WC_SMALL
+               : ((((1 << J) % 32) == 0 && ((1 << J) / 32) < C) ? WC_LARGE : WC_GENERIC);
+}
 
 // Per-pixel best trial (written by the search kernel, read by compaction).
 struct PixRec {
@@ -68,7 +77,10 @@ struct SearchParams {
     int32_t n_w;
     int32_t widths[kMaxW];
     int32_t wclass[kMaxW];
-    int32_t n_small, n_large;   // widths of the in-lane and lane-strided classes
+    int32_t pow2_wi[kPow2];     // width index of 2^j if it has a compile-time path, else -1
+    int32_t has_small, has_large;
+    int32_t n_gen;              // widths evaluated from shared memory
+    int32_t gen_wi[kMaxW];
     int32_t n_dm;
     int32_t new_blk;       // > 0: only trials that end in the last new_blk samples
     // ---- outputs (indexed by absolute pixel)

@@ -77,11 +77,21 @@ void base_params(const nsfrb_plan_s *pl, SearchParams &sp) {
     sp.table = pl->d_table;
     sp.n_deltas = pl->n_deltas;
     sp.n_w = c.n_w;
+    for (int j = 0; j < kPow2; ++j) sp.pow2_wi[j] = -1;
     for (int i = 0; i < c.n_w; ++i) {
         sp.widths[i] = pl->widths[i];
         sp.wclass[i] = pl->wclass[i];
-        sp.n_small += pl->wclass[i] == WC_SMALL;
-        sp.n_large += pl->wclass[i] == WC_LARGE;
+        const int w = pl->widths[i];
+        int j = -1;
+        for (int q = 0; q < kPow2; ++q)
+            if (w == (1 << q)) j = q;
+        if (pl->wclass[i] != WC_GENERIC && j >= 0) {
+            sp.pow2_wi[j] = i;
+            sp.has_small |= pl->wclass[i] == WC_SMALL;
+            sp.has_large |= pl->wclass[i] == WC_LARGE;
+        } else {
+            sp.gen_wi[sp.n_gen++] = i;
+        }
     }
     sp.n_dm = c.n_dm;
     sp.rec = pl->d_rec;
@@ -351,15 +361,11 @@ nsfrb_status nsfrb_plan(const nsfrb_config *cfg, nsfrb_plan_t *out) {
     int smax_active = 0;
     for (int u = 0; u < pl->n_u_active; ++u) smax_active = std::max(smax_active, info[u * kInfo + UI_SMAX]);
     pl->Tp = static_cast<int>(align_up(static_cast<size_t>(32 * pl->C + smax_active + 1), 4));
-    const int sh = std::min(pl->C, kSmallMax);
     for (int i = 0; i < c.n_w; ++i) {
         const int w = pl->widths[i];
-        if (w <= sh)
-            pl->wclass[i] = WC_SMALL;
-        else if (w % 32 == 0 && w / 32 < pl->C)
-            pl->wclass[i] = WC_LARGE;
-        else
-            pl->wclass[i] = WC_GENERIC;
+        pl->wclass[i] = WC_GENERIC;
+        for (int j = 0; j < kPow2; ++j)
+            if (w == (1 << j)) pl->wclass[i] = pow2_class(pl->C, j);
     }
     // The plan must fit at least the plain staging scheme in 227 KB.
     {

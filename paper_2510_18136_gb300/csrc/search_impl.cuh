@@ -186,21 +186,30 @@ static __device__ __noinline__ float warp_median(const float *v, int n, uint32_t
 
 // ------------------------------------------------------------------ boxcar building blocks
 
+// Three-input maximum (sm_100+ form of max.f32); NaN inputs are ignored like
+// the two-input form, so elements outside the valid range drop out.
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+// max over f(0..N-1) with four independent accumulators of 3-input maxima, so
+// that the reduction is four short dependency chains instead of one long one.
+template <int N, typename F>
+__device__ __forceinline__ float tree_max(F f) {
+    float acc[4] = {neg_inf(), neg_inf(), neg_inf(), neg_inf()};
+#pragma unroll
+    for (int j = 0; j + 1 < N; j += 2) acc[(j >> 1) & 3] = fmax3(acc[(j >> 1) & 3], f(j), f(j + 1));
+    if constexpr (N & 1) acc[3] = fmaxf(acc[3], f(N - 1));
+    return fmaxf(fmaxf(acc[0], acc[1]), fmaxf(acc[2], acc[3]));
+}
+
 // In-lane small width W: B[c] = P[t0+c+W] - P[t0+c] from the in-lane prefix Lp
 // (Lp[c] = sum of this lane's D[0..c)) and the halo H[i] = total + Lp_next[i].
 template <int C, int SH, int W>
 __device__ __forceinline__ float small_max_w(const float (&Lp)[C + 1], const float (&H)[SH + 1]) {
-    float m = neg_inf();
-#pragma unroll
-    for (int c = 0; c < C; ++c) {
-        float b;
-        if (c + W <= C)
-            b = Lp[c + W] - Lp[c];
-        else
-            b = H[c + W - C] - Lp[c];
-        m = fmaxf(m, b);
-    }
-    return m;
+    return tree_max<C>([&](int c) { return (c + W <= C) ? Lp[c + W] - Lp[c] : H[c + W - C] - Lp[c]; });
 }
 
 template <int C, int SH, int W>
@@ -222,21 +231,6 @@ __device__ __forceinline__ int small_find_w(const float (&Lp)[C + 1], const floa
 #define NSFRB_SMALL_CASES(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16)
 
 template <int C, int SH>
-__device__ __forceinline__ float small_max(int w, const float (&Lp)[C + 1], const float (&H)[SH + 1]) {
-    switch (w) {
-#define NSFRB_SC(W)                                                 \
-    case W:                                                         \
-        if constexpr (W <= SH) return small_max_w<C, SH, W>(Lp, H); \
-        break;
-        NSFRB_SMALL_CASES(NSFRB_SC)
-#undef NSFRB_SC
-        default:
-            break;
-    }
-    return neg_inf();
-}
-
-template <int C, int SH>
 __device__ __forceinline__ int small_find(int w, const float (&Lp)[C + 1], const float (&H)[SH + 1],
                                           float inv, float target, int t0) {
     switch (w) {
@@ -255,10 +249,7 @@ __device__ __forceinline__ int small_find(int w, const float (&Lp)[C + 1], const
 // Lane-strided width 32*M: Ps[i] = P[32 i + lane]; B = Ps[i+M] - Ps[i].
 template <int C, int M>
 __device__ __forceinline__ float large_max_m(const float (&Ps)[C]) {
-    float m = neg_inf();
-#pragma unroll
-    for (int i = 0; i + M < C; ++i) m = fmaxf(m, Ps[i + M] - Ps[i]);
-    return m;
+    return tree_max<C - M>([&](int i) { return Ps[i + M] - Ps[i]; });
 }
 
 template <int C, int M>
@@ -274,21 +265,6 @@ __device__ __forceinline__ int large_find_m(const float (&Ps)[C], float inv, flo
     X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16) X(17) \
     X(18) X(19) X(20) X(21) X(22) X(23) X(24) X(25) X(26) X(27) X(28) X(29) X(30) X(31) X(32)   \
     X(33) X(34) X(35) X(36) X(37) X(38)
-
-template <int C>
-__device__ __forceinline__ float large_max(int m, const float (&Ps)[C]) {
-    switch (m) {
-#define NSFRB_LC(M)                                        \
-    case M:                                                \
-        if constexpr (M < C) return large_max_m<C, M>(Ps); \
-        break;
-        NSFRB_LARGE_CASES(NSFRB_LC)
-#undef NSFRB_LC
-        default:
-            break;
-    }
-    return neg_inf();
-}
 
 template <int C>
 __device__ __forceinline__ int large_find(int m, const float (&Ps)[C], float inv, float target,
@@ -320,12 +296,25 @@ __device__ __forceinline__ int generic_find(const float *Pw, int w, int L, int t
     return INT_MAX;
 }
 
+#define NSFRB_POW2(X) X(0) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10)
+
 // In-lane prefix of this lane's chunk: Lp[c] = D[0] + ... + D[c-1]; returns the total.
+// Two independent half chains (the second half is summed from its own start and
+// then offset by the first half's total) halve the dependent-add latency.
 template <int C>
 __device__ __forceinline__ float lane_prefix(const float (&D)[C], float (&Lp)[C + 1]) {
+    constexpr int H1 = (C + 1) / 2;
     Lp[0] = 0.0f;
 #pragma unroll
-    for (int c = 0; c < C; ++c) Lp[c + 1] = Lp[c] + D[c];
+    for (int c = 0; c < H1; ++c) Lp[c + 1] = Lp[c] + D[c];
+    if constexpr (C > H1) {
+        float q[C - H1];
+        q[0] = D[H1];
+#pragma unroll
+        for (int j = 1; j < C - H1; ++j) q[j] = q[j - 1] + D[H1 + j];
+#pragma unroll
+        for (int j = 0; j < C - H1; ++j) Lp[H1 + 1 + j] = Lp[H1] + q[j];
+    }
     return Lp[C];
 }
 
@@ -570,49 +559,56 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel(const __grid_consta
                     if (lane == 0) carry = 0.0f;
 #pragma unroll
                     for (int c = 0; c < C; ++c) Pw[t0 + c] = carry + Lp[c];
-                    if (!masked && p.n_small > 0) {
-                        // small widths, in-lane
+                    if (!masked && p.has_small) {
+                        // power-of-two widths <= min(C, 16): in-lane, compile-time unrolled
                         float H[SH + 1];
                         lane_halo<C, SH>(Lp, tot, lane, H);
-#pragma unroll 1
-                        for (int wi = 0; wi < p.n_w; ++wi) {
-                            if (p.wclass[wi] != WC_SMALL) continue;
-                            const int w = p.widths[wi];
-                            const float m = small_max<C, SH>(w, Lp, H);
-                            consider(wi, m);
-                            if constexpr (FULL) {
-                                const float mw = warp_max(m), sw = mw * s_inv[wi];
-                                int t = INT_MAX;
-                                if (mw != neg_inf()) t = warp_min(small_find<C, SH>(w, Lp, H, s_inv[wi], sw, t0));
-                                write_full(wi, sw, t);
-                            }
-                        }
+#define NSFRB_SMALL_J(J)                                                                                   \
+    if constexpr (pow2_class(C, J) == WC_SMALL) {                                                         \
+        const int wi = p.pow2_wi[J];                                                                       \
+        if (wi >= 0) {                                                                                     \
+            const float m = small_max_w<C, SH, (1 << J)>(Lp, H);                                          \
+            consider(wi, m);                                                                               \
+            if constexpr (FULL) {                                                                          \
+                const float mw = warp_max(m), sw = mw * s_inv[wi];                                        \
+                int t = INT_MAX;                                                                           \
+                if (mw != neg_inf()) t = warp_min(small_find_w<C, SH, (1 << J)>(Lp, H, s_inv[wi], sw, t0)); \
+                write_full(wi, sw, t);                                                                     \
+            }                                                                                              \
+        }                                                                                                  \
+    }
+                        NSFRB_POW2(NSFRB_SMALL_J)
+#undef NSFRB_SMALL_J
                     }
                 }
                 __syncwarp();
-                if (!masked && p.n_large > 0) {
-                    // multiples of 32, lane-strided
+                if (!masked && p.has_large) {
+                    // power-of-two widths 32 * M with M < C: lane-strided, compile-time unrolled
                     float Ps[C];
 #pragma unroll
                     for (int i = 0; i < C; ++i) Ps[i] = Pw[32 * i + lane];
-#pragma unroll 1
-                    for (int wi = 0; wi < p.n_w; ++wi) {
-                        if (p.wclass[wi] != WC_LARGE) continue;
-                        const int mm = p.widths[wi] >> 5;
-                        const float m = large_max<C>(mm, Ps);
-                        consider(wi, m);
-                        if constexpr (FULL) {
-                            const float mw = warp_max(m), sw = mw * s_inv[wi];
-                            int t = INT_MAX;
-                            if (mw != neg_inf()) t = warp_min(large_find<C>(mm, Ps, s_inv[wi], sw, lane));
-                            write_full(wi, sw, t);
-                        }
-                    }
+#define NSFRB_LARGE_J(J)                                                                                   \
+    if constexpr (pow2_class(C, J) == WC_LARGE) {                                                         \
+        const int wi = p.pow2_wi[J];                                                                       \
+        if (wi >= 0) {                                                                                     \
+            const float m = large_max_m<C, ((1 << J) >> 5)>(Ps);                                          \
+            consider(wi, m);                                                                               \
+            if constexpr (FULL) {                                                                          \
+                const float mw = warp_max(m), sw = mw * s_inv[wi];                                        \
+                int t = INT_MAX;                                                                           \
+                if (mw != neg_inf()) t = warp_min(large_find_m<C, ((1 << J) >> 5)>(Ps, s_inv[wi], sw, lane)); \
+                write_full(wi, sw, t);                                                                     \
+            }                                                                                              \
+        }                                                                                                  \
+    }
+                    NSFRB_POW2(NSFRB_LARGE_J)
+#undef NSFRB_LARGE_J
                 }
-                // everything else from shared memory
+                // every other width (and every width of a masked search) from shared memory
+                const int n_gen = masked ? p.n_w : p.n_gen;
 #pragma unroll 1
-                for (int wi = 0; wi < p.n_w; ++wi) {
-                    if (!masked && p.wclass[wi] != WC_GENERIC) continue;
+                for (int g = 0; g < n_gen; ++g) {
+                    const int wi = masked ? g : p.gen_wi[g];
                     const int w = p.widths[wi];
                     const int tl = masked ? max(0, L - w - p.new_blk + 1) : 0;
                     const float m = generic_max(Pw, w, L, tl, lane);
