@@ -9,7 +9,7 @@
 
 namespace nsfrb {
 
-constexpr int kWarps = 8;                 // warps per search CTA
+constexpr int kWarps = 12;                // warps per search CTA
 constexpr int kThreads = kWarps * 32;     // threads per search CTA
 constexpr int kMaxW = 16;                 // widths per plan
 constexpr int kMaxSub = 32;               // subbands per plan
@@ -110,7 +110,8 @@ __host__ __device__ inline SmemLayout smem_layout(const SearchParams &p, int C) 
     L.pbuf = o;
     o += sizeof(float) * (size_t)kWarps * 32 * C;
     L.hist = o;
-    if (p.noise_mode == 1) o += sizeof(uint32_t) * (size_t)kWarps * kHistBins;
+    // MAD histograms: in the staging buffer of the current item when staging, else own space
+    if (p.noise_mode == 1 && p.stage != 2) o += sizeof(uint32_t) * (size_t)kWarps * kHistBins;
     L.wbest = o;
     o += sizeof(PixRec) * kWarps;
     L.sinv = o;

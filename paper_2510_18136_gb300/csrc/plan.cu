@@ -10,7 +10,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/nsfrb.h"
+#include "nsfrb.h"
 #include "nsfrb_internal.h"
 #include "plan_internal.h"
 

@@ -6,7 +6,7 @@
 
 #include <cuda_runtime.h>
 
-#include "../../include/nsfrb.h"
+#include "nsfrb.h"
 #include "nsfrb_internal.h"
 
 namespace nsfrb {

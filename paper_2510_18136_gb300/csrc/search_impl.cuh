@@ -448,12 +448,38 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel(const __grid_consta
             phase[sb] ^= 1u;
             if (!ok) atomicOr(&s_flag[0], ERR_WAIT_TIMEOUT);
             if (p.stage == 2) {
-                const unsigned short *stg =
-                    reinterpret_cast<const unsigned short *>(s_stg + (size_t)sb * n_sub * p.stg_pitch);
-                const int pitch = p.stg_pitch / 2;
-                for (int i = tid; i < n_sub * n_t; i += kThreads) {
-                    const int k = i / n_t, t = i - k * n_t;
-                    xs[(size_t)k * Tp + t] = widen16(stg[(size_t)k * pitch + stg_off + t], p.dtype);
+                const unsigned char *stg_b = s_stg + (size_t)sb * n_sub * p.stg_pitch;
+                if (stg_off == 0 && (n_t & 7) == 0) {
+                    // 8 samples per 16-byte word -> two float4 stores
+                    const int nv = n_t >> 3;
+                    for (int i = tid; i < n_sub * nv; i += kThreads) {
+                        const int k = i / nv, v = i - k * nv;
+                        const uint4 raw = *reinterpret_cast<const uint4 *>(stg_b + (size_t)k * p.stg_pitch + 16 * v);
+                        float4 a, c;
+                        if (p.dtype == 1) {
+                            a = make_float4(__uint_as_float(raw.x << 16), __uint_as_float(raw.x & 0xffff0000u),
+                                            __uint_as_float(raw.y << 16), __uint_as_float(raw.y & 0xffff0000u));
+                            c = make_float4(__uint_as_float(raw.z << 16), __uint_as_float(raw.z & 0xffff0000u),
+                                            __uint_as_float(raw.w << 16), __uint_as_float(raw.w & 0xffff0000u));
+                        } else {
+                            const float2 h0 = __half22float2(*reinterpret_cast<const __half2 *>(&raw.x));
+                            const float2 h1 = __half22float2(*reinterpret_cast<const __half2 *>(&raw.y));
+                            const float2 h2 = __half22float2(*reinterpret_cast<const __half2 *>(&raw.z));
+                            const float2 h3 = __half22float2(*reinterpret_cast<const __half2 *>(&raw.w));
+                            a = make_float4(h0.x, h0.y, h1.x, h1.y);
+                            c = make_float4(h2.x, h2.y, h3.x, h3.y);
+                        }
+                        float4 *dst = reinterpret_cast<float4 *>(xs + (size_t)k * Tp + 8 * v);
+                        dst[0] = a;
+                        dst[1] = c;
+                    }
+                } else {
+                    const unsigned short *stg = reinterpret_cast<const unsigned short *>(stg_b);
+                    const int pitch = p.stg_pitch / 2;
+                    for (int i = tid; i < n_sub * n_t; i += kThreads) {
+                        const int k = i / n_t, t = i - k * n_t;
+                        xs[(size_t)k * Tp + t] = widen16(stg[(size_t)k * pitch + stg_off + t], p.dtype);
+                    }
                 }
             }
         }
@@ -473,7 +499,8 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel(const __grid_consta
         // ---- robust normalisation per (pixel, subband) row (MAD mode)
         bool bad_pixel = false;
         if (p.noise_mode == 1) {
-            uint32_t *hist = s_hist + warp * kHistBins;
+            uint32_t *hist = (p.stage == 2 ? reinterpret_cast<uint32_t *>(s_stg + (size_t)sb * n_sub * p.stg_pitch)
+                                           : s_hist) + warp * kHistBins;
             for (int k = warp; k < n_sub; k += kWarps) {
                 float *row = xs + (size_t)k * Tp;
                 const float med = warp_median(row, n_t, hist);
@@ -560,16 +587,22 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel(const __grid_consta
 #pragma unroll
                     for (int c = 0; c < C; ++c) Pw[t0 + c] = carry + Lp[c];
                     if (!masked && p.has_small) {
-                        // power-of-two widths <= min(C, 16): in-lane, compile-time unrolled
+                        // power-of-two widths <= min(C, 16): in-lane, compile-time unrolled and
+                        // branch-free (absent widths are computed and masked); ascending width
+                        // order with a strict '>' keeps the smallest width index on ties
                         float H[SH + 1];
                         lane_halo<C, SH>(Lp, tot, lane, H);
 #define NSFRB_SMALL_J(J)                                                                                   \
     if constexpr (pow2_class(C, J) == WC_SMALL) {                                                         \
         const int wi = p.pow2_wi[J];                                                                       \
-        if (wi >= 0) {                                                                                     \
-            const float m = small_max_w<C, SH, (1 << J)>(Lp, H);                                          \
-            consider(wi, m);                                                                               \
-            if constexpr (FULL) {                                                                          \
+        const float m = small_max_w<C, SH, (1 << J)>(Lp, H);                                              \
+        const float s = (wi >= 0) ? m * s_inv[wi < 0 ? 0 : wi] : neg_inf();                              \
+        if (s > ls) {                                                                                      \
+            ls = s;                                                                                        \
+            lw = wi;                                                                                       \
+        }                                                                                                  \
+        if constexpr (FULL) {                                                                              \
+            if (wi >= 0) {                                                                                 \
                 const float mw = warp_max(m), sw = mw * s_inv[wi];                                        \
                 int t = INT_MAX;                                                                           \
                 if (mw != neg_inf()) t = warp_min(small_find_w<C, SH, (1 << J)>(Lp, H, s_inv[wi], sw, t0)); \
@@ -590,10 +623,14 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel(const __grid_consta
 #define NSFRB_LARGE_J(J)                                                                                   \
     if constexpr (pow2_class(C, J) == WC_LARGE) {                                                         \
         const int wi = p.pow2_wi[J];                                                                       \
-        if (wi >= 0) {                                                                                     \
-            const float m = large_max_m<C, ((1 << J) >> 5)>(Ps);                                          \
-            consider(wi, m);                                                                               \
-            if constexpr (FULL) {                                                                          \
+        const float m = large_max_m<C, ((1 << J) >> 5)>(Ps);                                              \
+        const float s = (wi >= 0) ? m * s_inv[wi < 0 ? 0 : wi] : neg_inf();                              \
+        if (s > ls) {                                                                                      \
+            ls = s;                                                                                        \
+            lw = wi;                                                                                       \
+        }                                                                                                  \
+        if constexpr (FULL) {                                                                              \
+            if (wi >= 0) {                                                                                 \
                 const float mw = warp_max(m), sw = mw * s_inv[wi];                                        \
                 int t = INT_MAX;                                                                           \
                 if (mw != neg_inf()) t = warp_min(large_find_m<C, ((1 << J) >> 5)>(Ps, s_inv[wi], sw, lane)); \
