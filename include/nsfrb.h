@@ -153,6 +153,36 @@ nsfrb_status nsfrb_full(nsfrb_plan_t plan, float *out_snr, int16_t *out_t_idx);
  * waits for the search.  ENOTREADY before the first search. */
 nsfrb_status nsfrb_last_timing(nsfrb_plan_t plan, float *search_ms, float *total_ms);
 
+/* ---- search without device allocation -------------------------------------
+ * The paper has no counterpart to this call.  It serves callers that cannot
+ * allocate device memory at search time: code that runs while another
+ * allocator (a framework's caching pool, a fixed real-time memory map) owns
+ * all free device memory, or a latency-bound loop that cannot afford
+ * cudaMalloc (which may synchronise the device).  It runs the same search and
+ * candidate compaction as nsfrb_search + nsfrb_candidates, but its scratch
+ * (delay tables, per-pixel best records, counters) lives in one fixed
+ * array inside the library, held by every GPU that loads the library until
+ * the process exits.  It calls no cudaMalloc, cudaFree or other allocating
+ * routine; the plan must have been made by nsfrb_plan (host memory only).
+ *
+ * d_cube, d_sigma: as nsfrb_search (device pointers, contiguous).
+ * d_out[cap]:      device buffer for the candidates (pixel order); only the
+ *                  first cap are written.
+ * d_n_total:       device int32: the full candidate count, or -1 if a zero
+ *                  MAD row was met (MAD mode), -2 if a bulk copy timed out.
+ * Asynchronous on `stream`.  Limits: ny*nx <= NSFRB_STATIC_MAX_PIX and the
+ * plan's tables <= NSFRB_STATIC_MAX_TABLE_WORDS int32 words (EINVAL beyond);
+ * candidate output mode only; no re-scoring.  The first call on a device
+ * looks up the array's device address there (and sets the kernel's shared
+ * memory limit), so make that first call before any stream capture.  Every
+ * call shares the one array and overwrites what the previous call left in
+ * it: calls whose work overlaps on the GPU (different streams, or different
+ * plans at once) race and must be serialised by the caller. */
+#define NSFRB_STATIC_MAX_PIX 262144
+#define NSFRB_STATIC_MAX_TABLE_WORDS 65536
+nsfrb_status nsfrb_search_static(nsfrb_plan_t plan, const void *d_cube, const float *d_sigma,
+                                 nsfrb_candidate *d_out, int32_t cap, int32_t *d_n_total, void *stream);
+
 /* ---- serving (Sec. 2.2: real-time search of 25-sample blocks arriving every
  * 3.35 s, with a 3.35 s timeout for missing subband images) ---------------
  * A plan opened for streaming keeps a rolling on-device window of the last

@@ -73,6 +73,8 @@ nsfrb_status queue_search(nsfrb_plan_s *pl, const void *cube, int64_t cube_pix0,
                           const int32_t *t_off_dev = nullptr);
 size_t elem_size(int dtype);
 void destroy_stream_state(nsfrb_plan_s *pl);
+void base_params(const nsfrb_plan_s *pl, SearchParams &sp);
+bool choose_stage(const nsfrb_plan_s *pl, SearchParams &sp, size_t &smem);
 
 cudaError_t launch_search_c1(const SearchParams &, int, size_t, cudaStream_t);
 cudaError_t launch_search_c3(const SearchParams &, int, size_t, cudaStream_t);

@@ -66,6 +66,7 @@ def _load() -> ctypes.CDLL:
         "nsfrb_best": ([P, P, P], c_int32),
         "nsfrb_full": ([P, P, P], c_int32),
         "nsfrb_last_timing": ([P, POINTER(c_float), POINTER(c_float)], c_int32),
+        "nsfrb_search_static": ([P, P, P, P, c_int32, P, P], c_int32),
         "nsfrb_stream_open": ([P, c_int32, c_size_t], c_int32),
         "nsfrb_stream_bytes": ([P, c_int32, POINTER(c_size_t)], c_int32),
         "nsfrb_stream_push": ([P, P, c_uint32], c_int32),
