@@ -1,0 +1,121 @@
+"""Serving loop (rolling window, block push, masked search, CUDA graph) vs the oracle.
+
+After each pushed block the streamed candidates must equal the oracle's search
+of the current window restricted to the trials that end in the newest block
+(t + w - 1 + smax_d >= n_t - n_blk).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2510_18136_gb300 import synth
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def native():
+    from paper_2510_18136_gb300 import build
+    build.build()
+    from paper_2510_18136_gb300 import native as nat
+    assert torch.cuda.is_available()
+    return nat
+
+
+def _series(cfg, n_total, seed, n_inj=5):
+    """A long pixel-major series [n_pix, n_sub, n_total] with pulses spread over time."""
+    long_cfg = synth.SearchConfig(ny=cfg.ny, nx=cfg.nx, n_t=n_total, freq_mhz=cfg.freq_mhz, dm=cfg.dm,
+                                  widths=cfg.widths)
+    x = synth.plain_noise(long_cfg, seed)
+    raw = synth.draw_injections(long_cfg, n_inj, seed + 1, dm_range=(0.0, float(cfg.dm[-1])),
+                                snr_range=(8.0, 20.0), max_width=32, min_sep=1)
+    sh = oracle.delay_table(cfg.freq_mhz, raw["dm"])
+    inj = synth.place_injections(raw, sh, n_total, cfg.n_sub, 1.0)
+    synth.add_injections(x, long_cfg, inj, sh)
+    return x
+
+
+def _window_oracle(cfg, window, n_blk, tab):
+    smax = tab.max(axis=1)
+    t_lo = np.array([[cfg.n_t - n_blk - int(w) + 1 - int(s) for w in cfg.widths] for s in smax], np.int32)
+    res, best, _ = oracle.search_cube(window, tab, cfg.widths, sigma=4.0, t_lo=t_lo)
+    return best
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_stream_equals_masked_window_search(native, dtype):
+    cfg = synth.SearchConfig(ny=5, nx=7, n_t=96, dm=np.linspace(0, 1500, 20),
+                             widths=np.array([1, 2, 4, 8, 16, 32, 50], np.int32), threshold=5.0)
+    n_blk, n_blocks = 12, 14
+    x = _series(cfg, n_blk * n_blocks, 3)
+    if dtype == "bf16":
+        x = x.to(torch.bfloat16).to(torch.float32)
+    tab = oracle.delay_table(cfg.freq_mhz, cfg.dm)
+    plan = native.Plan(cfg, dtype=dtype)
+    plan.stream_open(n_blk)
+    xn = x.numpy()
+    total = 0
+    for b in range(n_blocks):
+        blk = torch.from_numpy(xn[:, :, b * n_blk:(b + 1) * n_blk].transpose(2, 1, 0).copy())
+        blk = blk.reshape(n_blk, cfg.n_sub, cfg.ny, cfg.nx).contiguous()
+        plan.stream_push(blk)
+        cand, lat = plan.stream_poll(timeout_ms=10000)
+        assert lat > 0.0
+        end = (b + 1) * n_blk
+        window = np.zeros((cfg.n_pix, cfg.n_sub, cfg.n_t), np.float32)
+        lo = max(0, end - cfg.n_t)
+        window[:, :, cfg.n_t - (end - lo):] = xn[:, :, lo:end]
+        best = _window_oracle(cfg, window, n_blk, tab)
+        parity.compare_candidates(cand, best, cfg.threshold, np.arange(cfg.n_pix), cfg.nx)
+        total += len(cand)
+    assert total > 0
+    assert plan.stream_blocks() == n_blocks
+    plan.close()
+
+
+def test_stream_missing_subband_is_zero_filled(native):
+    cfg = synth.SearchConfig(ny=3, nx=4, n_t=48, dm=np.linspace(0, 1000, 9),
+                             widths=np.array([1, 2, 4, 8], np.int32), threshold=3.0)
+    n_blk = 8
+    x = _series(cfg, n_blk * 8, 11, n_inj=3).numpy()
+    tab = oracle.delay_table(cfg.freq_mhz, cfg.dm)
+    plan = native.Plan(cfg)
+    plan.stream_open(n_blk)
+    seen = x.copy()
+    for b in range(8):
+        mask = (1 << 16) - 1
+        if b == 6:
+            mask &= ~(1 << 3)
+            seen[:, 3, b * n_blk:(b + 1) * n_blk] = 0.0
+        blk = torch.from_numpy(x[:, :, b * n_blk:(b + 1) * n_blk].transpose(2, 1, 0).copy())
+        plan.stream_push(blk.reshape(n_blk, 16, cfg.ny, cfg.nx).contiguous(), present_mask=mask)
+        cand, _ = plan.stream_poll(timeout_ms=10000)
+        end = (b + 1) * n_blk
+        window = np.zeros((cfg.n_pix, 16, cfg.n_t), np.float32)
+        lo = max(0, end - cfg.n_t)
+        window[:, :, cfg.n_t - (end - lo):] = seen[:, :, lo:end]
+        best = _window_oracle(cfg, window, n_blk, tab)
+        parity.compare_candidates(cand, best, cfg.threshold, np.arange(cfg.n_pix), cfg.nx)
+    plan.close()
+
+
+def test_stream_admission_and_protocol_errors(native):
+    cfg = synth.SearchConfig(ny=4, nx=4, n_t=64, dm=np.array([0.0, 500.0]), widths=np.array([1, 4], np.int32))
+    plan = native.Plan(cfg)
+    with pytest.raises(native.NsfrbError) as e:
+        plan.stream_open(8, hbm_reserve=1 << 60)    # admission: more than the device has
+    assert e.value.status == native.ENOMEM
+    plan.stream_open(8)
+    with pytest.raises(native.NsfrbError) as e:
+        plan.stream_poll(timeout_ms=10)              # nothing pushed yet
+    assert e.value.status == native.ENOTREADY
+    blk = torch.randn((8, 16, 4, 4))
+    plan.stream_push(blk)
+    with pytest.raises(native.NsfrbError) as e:
+        plan.stream_push(blk)                        # previous block not polled
+    assert e.value.status == native.ENOTREADY
+    plan.stream_poll(timeout_ms=10000)
+    assert plan.stream_bytes(8) > 0
+    plan.close()
