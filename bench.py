@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--nx", type=int, default=301)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving-blocks", type=int, default=40,
+                    help="blocks per field of the 4-field serving latency run (0: skip)")
     ap.add_argument("--seed", type=int, default=0)
     return ap.parse_args()
 
@@ -81,6 +83,22 @@ def make_cube(native, synth, cfg, seed, device, dtype):
     if dtype == "bf16":
         cube = cube.to(torch.bfloat16)
     return cube, inj
+
+
+# DRAM bytes (read + write) per 301x301 FP32 launch from the ncu capture summarised in
+# profiles/search_kernel_full_window.md, valid for the kernel source with this sha256 prefix.
+NCU_TRAFFIC = {"sha256_16": "591f2879b6f4752f", "bytes": 7.034e9, "workload": (301, 301, "f32")}
+
+
+def measured_traffic(ny, nx, dtype):
+    """ncu traffic per launch if it was taken on the current kernel source, else None."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_2510_18136_gb300", "csrc", "search_impl.cuh")
+    with open(src, "rb") as fh:
+        digest = hashlib.sha256(fh.read()).hexdigest()[:16]
+    if digest != NCU_TRAFFIC["sha256_16"] or (ny, nx, dtype) != NCU_TRAFFIC["workload"]:
+        return None
+    return NCU_TRAFFIC["bytes"]
 
 
 def alg_ops(cfg, plan):
@@ -176,9 +194,13 @@ def oracle_sample_rate(cube_host, cfg, target_s: float, seed: int = 0):
         oracle.search_cube(x, tab, cfg.widths, sigma=sig)
         return time.perf_counter() - t0
 
-    t = run(16)
-    n = int(min(cfg.n_pix, max(16, 16 * target_s / max(t, 1e-3))))
+    n = 256
     t = run(n)
+    for _ in range(2):   # calibrate the sample to about target_s seconds
+        n = int(min(cfg.n_pix, max(16, n * target_s / max(t, 1e-3))))
+        t = run(n)
+        if t > 0.5 * target_s or n == cfg.n_pix:
+            break
     trials = n * len(cfg.dm) * len(cfg.widths)
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return trials / t, n, t, cores
@@ -213,6 +235,43 @@ def reference_arm(args):
             "e2e": {"value": value, "unit": "trials/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+# ----------------------------------------------------------------------------- serving
+
+SERVING_FIELDS = ((301, 301), (257, 257), (193, 193), (129, 129))
+
+
+def serving_latency(native, synth, n_blocks: int, seed: int = 0):
+    """Four concurrent fields (one plan, stream and CUDA graph each), BF16 window of 1200
+    samples, 25-sample blocks pushed back to back (unpaced); push -> candidates device latency."""
+    import torch
+    fields = []
+    for i, (ny, nx) in enumerate(SERVING_FIELDS):
+        cfg = synth.config_full_window(ny, nx)
+        plan = native.Plan(cfg, dtype="bf16")
+        plan.stream_open(25)
+        g = torch.Generator().manual_seed(seed + i)
+        blocks = [torch.randn((25, cfg.n_sub, ny, nx), generator=g).pin_memory() for _ in range(2)]
+        fields.append((cfg, plan, blocks))
+    lat = []
+    t0 = time.perf_counter()
+    for b in range(n_blocks):
+        for cfg, plan, blocks in fields:
+            plan.stream_push(blocks[b % 2])
+        for cfg, plan, blocks in fields:
+            _, ms = plan.stream_poll(timeout_ms=3350)
+            if b >= 2:
+                lat.append(ms)
+    wall = time.perf_counter() - t0
+    for _, plan, _ in fields:
+        plan.close()
+    lat = np.array(lat)
+    return {"fields": [f"{ny}x{nx}" for ny, nx in SERVING_FIELDS], "storage": "bf16", "block_samples": 25,
+            "window_samples": 1200, "blocks_per_field": n_blocks, "paced": False,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "max_ms": float(lat.max()), "blocks_per_s": 4 * n_blocks / wall,
+            "cadence_s": 3.355}
 
 
 # ----------------------------------------------------------------------------- GPU arm
@@ -295,6 +354,10 @@ def main():
         dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
     e2e_value = world * args.e2e_steps * cfg.n_trials / float(e2e_t.item())
 
+    serving = None
+    if args.serving_blocks > 0 and rank == 0:
+        serving = serving_latency(native, synth, args.serving_blocks, seed=args.seed)
+
     pk = peaks()
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     kern_s = statistics.mean(search_ms) / 1e3
@@ -311,7 +374,8 @@ def main():
                    "storage": args.dtype, "noise": "known sigma", "l2": "inputs larger than L2 (cube "
                    f"{alg_bytes / 1e9:.2f} GB)", "parallelism": f"replicas x{world} (pixels of one cube per GPU)"},
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
-                     "unit": "TFLOP/s", "frac": achieved / peak_ops, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / peak_ops,
+                     "traffic": measured_traffic(cfg.ny, cfg.nx, args.dtype),
                      "kernel": "search_kernel", "kernel_ms": kern_s * 1e3,
                      "ops_per_launch": ops, "peak_basis": f"{n_sm} SM x 128 FP32 lanes x "
                      f"{pk['sm_max_mhz']:.0f} MHz ({pk['source']} max clock)"},
@@ -321,7 +385,8 @@ def main():
                 "d2h_bytes_per_step": 8 + 24 * n_c},
         "gpu_launches": 3 * args.steps,
         "candidates": int(len(cand)), "injections": int(len(inj)),
-        "p99_block_latency_ms": None,
+        "p99_block_latency_ms": None if serving is None else serving["p99_ms"],
+        "serving": serving,
         "clocks": ck,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
