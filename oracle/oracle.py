@@ -24,6 +24,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "nsfrb_oracle.c")
+_SRC_CNN = os.path.join(_HERE, "cnn_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
@@ -39,11 +40,12 @@ __all__ = [
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (-O2 -fopenmp); returns the .so path."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_CNN))
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < newest:
         tmp = _SO + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared",
                                "-fno-fast-math", "-ffp-contract=off",
-                               _SRC, "-o", tmp, "-lm"])
+                               _SRC, _SRC_CNN, "-o", tmp, "-lm"])
         os.replace(tmp, _SO)
     return _SO
 
@@ -63,6 +65,19 @@ def _load():
                                        ctypes.c_int, P, ctypes.c_int, P, P, ctypes.c_int,
                                        P, P, P]
             lib.orc_search.restype = None
+            lib.orc_cnn_n_params.argtypes = [P]
+            lib.orc_cnn_n_params.restype = ctypes.c_int64
+            lib.orc_cnn_forward_backward.argtypes = [P, P, P, P, P, ctypes.c_double, ctypes.c_int,
+                                                     P, P, P, P]
+            lib.orc_cnn_forward_backward.restype = ctypes.c_double
+            lib.orc_philox4x32_10.argtypes = [P, P, P]
+            lib.orc_philox4x32_10.restype = None
+            lib.orc_dropout_mask.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_uint32,
+                                             ctypes.c_uint64, P]
+            lib.orc_dropout_mask.restype = None
+            lib.orc_adam.argtypes = [ctypes.c_int64, P, P, P, P, ctypes.c_int, ctypes.c_double,
+                                     ctypes.c_double, ctypes.c_double, ctypes.c_double]
+            lib.orc_adam.restype = None
             _lib = lib
     return _lib
 

@@ -1,0 +1,143 @@
+"""Pins of the FP64 classifier oracle (Sec. 2.3 classifier) against library
+routines (torch float64 autograd), central finite differences and published
+Philox known-answer vectors."""
+import os
+
+import numpy as np
+import pytest
+import torch
+import torch.nn.functional as F
+
+import oracle  # noqa: F401  (builds the library)
+from oracle import cnn
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+DIMS = cnn.CnnDims(B=3, D=16, H=16, W=32, C0=2, C=(2, 3, 3, 4), F=3)
+
+
+def _params(dims, seed):
+    rng = np.random.default_rng(seed)
+    p = np.empty(cnn.n_params(dims))
+    for name, o, shape in cnn.layout(dims):
+        n = int(np.prod(shape))
+        if name.endswith("gamma"):
+            p[o:o + n] = rng.uniform(0.5, 1.5, n)
+        else:
+            p[o:o + n] = rng.normal(0.0, 0.4, n)
+    return p
+
+
+def _torch_model(dims, params, x, labels, keep=None, p=0.0):
+    """The same network written with torch.nn.functional in float64 (NCDHW)."""
+    P = torch.tensor(params, dtype=torch.float64, requires_grad=True)
+    t = {name: P[o:o + int(np.prod(shape))].reshape(shape) for name, o, shape in cnn.layout(dims)}
+    h = torch.tensor(x, dtype=torch.float64).permute(0, 4, 1, 2, 3)
+    for l in range(4):
+        w = t[f"conv{l}.w"].permute(0, 4, 1, 2, 3)          # [Co, Ci, kz, ky, kx]
+        h = F.conv3d(h, w, padding=1)
+        h = F.batch_norm(h, None, None, t[f"bn{l}.gamma"], t[f"bn{l}.beta"], training=True, eps=1e-5)
+        h = F.max_pool3d(F.relu(h), 2)
+    feat = h.permute(0, 2, 3, 4, 1).reshape(dims.B, -1)       # flatten (d, h, w, c)
+    h1 = F.relu(feat @ t["fc1.w"].T + t["fc1.b"])
+    if keep is not None:
+        h1 = h1 * torch.tensor(keep, dtype=torch.float64) / (1.0 - p)
+    z = h1 @ t["fc2.w"] + t["fc2.b"]
+    loss = F.binary_cross_entropy_with_logits(z, torch.tensor(labels, dtype=torch.float64))
+    loss.backward()
+    return loss.item(), z.detach().numpy(), P.grad.numpy()
+
+
+def test_philox_known_answers():
+    with open(os.path.join(GOLDEN, "philox_kat.txt")) as fh:
+        for line in fh:
+            if line.startswith("#") or not line.strip():
+                continue
+            v = [int(s, 16) for s in line.split()]
+            np.testing.assert_array_equal(cnn.philox4x32_10(v[0:4], v[4:6]), np.array(v[6:10], np.uint32))
+
+
+def test_dropout_mask_rate():
+    keep = cnn.dropout_mask(64, 128, 0.5, 7, 12345)
+    assert abs(keep.mean() - 0.5) < 0.02
+    assert (keep != cnn.dropout_mask(64, 128, 0.5, 8, 12345)).any()
+
+
+@pytest.mark.parametrize("with_dropout", [False, True])
+def test_forward_and_gradients_match_torch_float64(with_dropout):
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal((DIMS.B, DIMS.D, DIMS.H, DIMS.W, DIMS.C0))
+    labels = np.array([0.0, 1.0, 1.0])
+    params = _params(DIMS, 1)
+    keep = cnn.dropout_mask(DIMS.B, DIMS.F, 0.3, 3, 99) if with_dropout else None
+    p = 0.3 if with_dropout else 0.0
+    out = cnn.forward_backward(DIMS, params, x, labels, keep=keep, p=p)
+    l_ref, z_ref, g_ref = _torch_model(DIMS, params, x, labels, keep, p)
+    assert out["loss"] == pytest.approx(l_ref, rel=1e-10)
+    np.testing.assert_allclose(out["logits"], z_ref, rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(out["grads"], g_ref, rtol=1e-8, atol=1e-11)
+
+
+def test_gradients_by_central_differences():
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal((DIMS.B, DIMS.D, DIMS.H, DIMS.W, DIMS.C0))
+    labels = np.array([1.0, 0.0, 1.0])
+    params = _params(DIMS, 2)
+    g = cnn.forward_backward(DIMS, params, x, labels)["grads"]
+    h = 1e-6
+    for i in rng.choice(params.size, size=25, replace=False):
+        pp, pm = params.copy(), params.copy()
+        pp[i] += h
+        pm[i] -= h
+        num = (cnn.forward_backward(DIMS, pp, x, labels, grads=False)["loss"] -
+               cnn.forward_backward(DIMS, pm, x, labels, grads=False)["loss"]) / (2 * h)
+        assert num == pytest.approx(g[i], rel=1e-4, abs=1e-7), i
+
+
+def test_eval_mode_uses_running_statistics():
+    rng = np.random.default_rng(8)
+    x = rng.standard_normal((DIMS.B, DIMS.D, DIMS.H, DIMS.W, DIMS.C0))
+    params = _params(DIMS, 3)
+    nc = sum(DIMS.C)
+    rm, rv = rng.normal(0, 0.2, nc), rng.uniform(0.5, 2.0, nc)
+    out = cnn.forward_backward(DIMS, params, x, train=False, run_mean=rm, run_var=rv, grads=False)
+    P = torch.tensor(params)
+    t = {name: P[o:o + int(np.prod(shape))].reshape(shape) for name, o, shape in cnn.layout(DIMS)}
+    h = torch.tensor(x).permute(0, 4, 1, 2, 3)
+    c0 = 0
+    for l in range(4):
+        h = F.conv3d(h, t[f"conv{l}.w"].permute(0, 4, 1, 2, 3), padding=1)
+        c = DIMS.C[l]
+        h = F.batch_norm(h, torch.tensor(rm[c0:c0 + c]), torch.tensor(rv[c0:c0 + c]), t[f"bn{l}.gamma"],
+                         t[f"bn{l}.beta"], training=False, eps=1e-5)
+        h = F.max_pool3d(F.relu(h), 2)
+        c0 += c
+    feat = h.permute(0, 2, 3, 4, 1).reshape(DIMS.B, -1)
+    z = F.relu(feat @ t["fc1.w"].T + t["fc1.b"]) @ t["fc2.w"] + t["fc2.b"]
+    np.testing.assert_allclose(out["logits"], z.numpy(), rtol=1e-10, atol=1e-12)
+
+
+def test_batch_statistics_returned_unbiased():
+    rng = np.random.default_rng(9)
+    x = rng.standard_normal((DIMS.B, DIMS.D, DIMS.H, DIMS.W, DIMS.C0))
+    params = _params(DIMS, 4)
+    out = cnn.forward_backward(DIMS, params, x, labels=np.zeros(3), grads=False)
+    P = torch.tensor(params)
+    w0 = P[:DIMS.C[0] * 27 * DIMS.C0].reshape(DIMS.C[0], 3, 3, 3, DIMS.C0).permute(0, 4, 1, 2, 3)
+    y = F.conv3d(torch.tensor(x).permute(0, 4, 1, 2, 3), w0, padding=1)
+    np.testing.assert_allclose(out["run_mean"][:DIMS.C[0]], y.mean(dim=(0, 2, 3, 4)).numpy(), rtol=1e-10)
+    np.testing.assert_allclose(out["run_var"][:DIMS.C[0]], y.var(dim=(0, 2, 3, 4), unbiased=True).numpy(),
+                               rtol=1e-10)
+
+
+def test_adam_matches_torch():
+    rng = np.random.default_rng(1)
+    p0 = rng.standard_normal(50)
+    p, m, v = p0.copy(), np.zeros(50), np.zeros(50)
+    tp = torch.tensor(p0, requires_grad=True)
+    opt = torch.optim.Adam([tp], lr=1e-2, betas=(0.9, 0.999), eps=1e-8)
+    for t in range(1, 6):
+        g = rng.standard_normal(50)
+        cnn.adam(p, g, m, v, t, lr=1e-2)
+        tp.grad = torch.tensor(g)
+        opt.step()
+    np.testing.assert_allclose(p, tp.detach().numpy(), rtol=1e-12, atol=1e-14)
