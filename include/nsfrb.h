@@ -217,6 +217,78 @@ nsfrb_status nsfrb_stream_poll(nsfrb_plan_t plan, int32_t timeout_ms, nsfrb_cand
  * partly empty: their missing samples are zero). */
 nsfrb_status nsfrb_stream_blocks(nsfrb_plan_t plan, int64_t *n_blocks);
 
+/* ---- candidate classifier (Sec. 2.3: convolutional blocks with batch
+ * normalisation, a non-linearity and max-pooling, a small fully connected
+ * head with dropout, one logit per candidate interpreted through a sigmoid as
+ * the RFI probability p_rfi; binary cross-entropy; Adam) ------------------
+ * Network: 4 x {conv3d 3x3x3 (padding 1, no bias) -> batch norm -> ReLU ->
+ * max-pool 2x2x2} over cutouts [d][h][w][c0] (time, rows, cols, subbands as
+ * channels, BF16, channels last), then FC(f) -> ReLU -> dropout -> FC(1).
+ * Convolutions run as BF16 tensor-core GEMMs with FP32 accumulation; the
+ * parameters, batch-norm statistics, head, loss and Adam are FP32.
+ * Parameter vector layout (FP32, flat): for l = 0..3: W_l[c_l][27][c_{l-1}]
+ * (tap k = (kz*3+ky)*3+kx), gamma_l[c_l], beta_l[c_l]; then fc1_w[f][fin],
+ * fc1_b[f], fc2_w[f], fc2_b[1], fin = d/16 * h/16 * w/16 * c_3.
+ * Dropout keeps hidden unit (b, j) at training step s iff the first word of
+ * Philox4x32-10 (counter (b*f + j, s, 0, 0), key = seed) >> 8, times 2^-24,
+ * is >= dropout; kept units are scaled by 1/(1 - dropout). */
+typedef struct nsfrb_clf_s *nsfrb_clf_t;
+
+typedef struct {
+    int32_t batch;          /* largest batch per call                              */
+    int32_t d, h, w;        /* cutout time samples, rows, columns (multiples of 16) */
+    int32_t c0;             /* subbands = input channels (multiple of 8)            */
+    int32_t c[4];           /* channels of the four conv blocks (multiples of 8)    */
+    int32_t f;              /* hidden units of the head (1..1024)                   */
+    float dropout;          /* dropout rate of the hidden units, [0, 1)             */
+    uint64_t seed;          /* dropout key                                          */
+    float lr, beta1, beta2, eps;   /* Adam                                          */
+    float bn_momentum;      /* running statistics: r <- (1-m) r + m batch value
+                               (variance: unbiased)                                 */
+} nsfrb_clf_config;
+
+/* Create a classifier (device memory for the batch size; parameters zero,
+ * running mean 0 and variance 1, Adam state zero, step 0).  EINVAL, ENOMEM. */
+nsfrb_status nsfrb_clf_create(const nsfrb_clf_config *cfg, nsfrb_clf_t *out);
+nsfrb_status nsfrb_clf_n_params(nsfrb_clf_t clf, int64_t *n);
+/* Host copies of the flat FP32 parameter vector / the gradient of the last
+ * training step / the running statistics ([sum c_l] each, block after block). */
+nsfrb_status nsfrb_clf_set_params(nsfrb_clf_t clf, const float *h_params);
+nsfrb_status nsfrb_clf_get_params(nsfrb_clf_t clf, float *h_params);
+nsfrb_status nsfrb_clf_get_grads(nsfrb_clf_t clf, float *h_grads);
+nsfrb_status nsfrb_clf_get_bn_stats(nsfrb_clf_t clf, float *h_run_mean, float *h_run_var);
+nsfrb_status nsfrb_clf_set_bn_stats(nsfrb_clf_t clf, const float *h_run_mean, const float *h_run_var);
+
+/* One training step on d_x[batch][d][h][w][c0] (BF16, device) with labels
+ * d_labels[batch] (FP32 0 = astrophysical, 1 = artefact): forward with batch
+ * statistics (running statistics updated), mean BCE, backward into the
+ * gradient vector, and, if update != 0, one Adam step (then the step counter,
+ * which also indexes the dropout masks, advances).  *h_loss (optional, waits)
+ * receives the batch loss.  Asynchronous otherwise. */
+nsfrb_status nsfrb_clf_train_step(nsfrb_clf_t clf, const void *d_x, const float *d_labels, int32_t batch,
+                                  int32_t update, float *h_loss, void *stream);
+
+/* Inference (running statistics, no dropout): d_logit[batch] (device);
+ * p_rfi = 1 / (1 + exp(-logit)). */
+nsfrb_status nsfrb_clf_infer(nsfrb_clf_t clf, const void *d_x, int32_t batch, float *d_logit, void *stream);
+
+/* Cutouts around candidates of a plan's cube: d_out[n][d][h][w][n_sub] BF16.
+ * The window is centred on the candidate pixel and on t_idx + (w + smax)/2
+ * (w its width, smax its DM's largest shift); time is averaged in bins of
+ * b = max(1, ceil((w + smax) / (d/2))) samples so that the dispersed pulse
+ * spans at most half the cutout; values are divided by the candidate pixel's
+ * noise per subband and sample (sigma_D / sqrt(n_sub); d_sigma NULL: 1);
+ * zero outside the image and the window.  d_cube as for nsfrb_search. */
+nsfrb_status nsfrb_clf_cutouts(nsfrb_plan_t plan, const void *d_cube, const float *d_sigma,
+                               const nsfrb_candidate *d_cand, int32_t n, int32_t d, int32_t h, int32_t w,
+                               void *d_out, void *stream);
+
+/* Checkpoint: configuration, parameters, Adam state, running statistics and
+ * the step counter, to / from a binary file.  EINVAL on a mismatched file. */
+nsfrb_status nsfrb_clf_save(nsfrb_clf_t clf, const char *path);
+nsfrb_status nsfrb_clf_load(nsfrb_clf_t clf, const char *path);
+void nsfrb_clf_destroy(nsfrb_clf_t clf);
+
 /* Release everything the plan owns (device memory, streams, graphs). */
 void nsfrb_destroy(nsfrb_plan_t plan);
 

@@ -1,0 +1,204 @@
+// BF16 tensor-core GEMM with FP32 accumulation for the classifier's
+// convolutions (implicit in im2col form) and their gradients.
+//
+//   NT:  C[M][N]  = A[M][K] * B[N][K]^T      (A, B K-contiguous)
+//   TN:  C[M][N] += A[K][M]^T * B[K][N]      (A, B contiguous along M / N; split-K
+//                                             partial sums added atomically)
+//
+// Tiles of BM x BN x 32 are staged in shared memory with 16-byte cp.async
+// (zero-filled outside the matrix, double buffered) and fed to
+// mma.m16n8k16 through ldmatrix (.trans for the TN layout).  K must be a
+// multiple of 8 and every row start 16-byte aligned.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_bf16.h>
+
+namespace nsfrb {
+namespace gemm {
+
+constexpr int BK = 32;
+constexpr int kThreads = 128;   // 4 warps
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, bool pred) {
+    const int n = pred ? 16 : 0;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(n)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3, const void *p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(smem_u32(p)));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3, const void *p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(smem_u32(p)));
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// TRANS = false: A tile stored [BM][BK+8], B tile [BN][BK+8] (K contiguous)
+// TRANS = true:  A tile stored [BK][BM+8], B tile [BK][BN+8] (M / N contiguous)
+template <int BM, int BN, bool TRANS>
+struct Smem {
+    static constexpr int A_ELEMS = TRANS ? BK * (BM + 8) : BM * (BK + 8);
+    static constexpr int B_ELEMS = TRANS ? BK * (BN + 8) : BN * (BK + 8);
+    __nv_bfloat16 a[2][A_ELEMS];
+    __nv_bfloat16 b[2][B_ELEMS];
+};
+
+// One CTA computes a BM x BN tile of C over the K range [k_lo, k_hi).
+template <int BM, int BN, bool TRANS>
+__global__ void __launch_bounds__(kThreads) gemm_kernel(int M, int N, int K, const __nv_bfloat16 *__restrict__ A,
+                                                        int64_t lda, const __nv_bfloat16 *__restrict__ B,
+                                                        int64_t ldb, float *__restrict__ C, int64_t ldc,
+                                                        int k_split) {
+    constexpr int WM = (BN >= 64) ? 2 : 4;    // warps along M
+    constexpr int WN = 4 / WM;                // warps along N
+    constexpr int TM = BM / WM, TN = BN / WN; // warp tile
+    constexpr int MI = TM / 16, NI = TN / 8;
+    static_assert(NI % 2 == 0, "warp tile N must be a multiple of 16");
+    __shared__ __align__(128) Smem<BM, BN, TRANS> sm;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp % WM, wn = warp / WM;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    // K range of this CTA (split-K along gridDim.z, in whole BK steps)
+    const int k_steps = (K + BK - 1) / BK;
+    const int per = (k_steps + k_split - 1) / k_split;
+    const int ks0 = blockIdx.z * per, ks1 = min(k_steps, ks0 + per);
+    if (ks0 >= ks1) return;
+
+    auto load_tile = [&](int stage, int ks) {
+        const int kb = ks * BK;
+        if (!TRANS) {
+            // A: BM rows x 4 chunks of 8 along K
+            for (int c = tid; c < BM * (BK / 8); c += kThreads) {
+                const int r = c / (BK / 8), kc = (c % (BK / 8)) * 8;
+                const int gm = m0 + r, gk = kb + kc;
+                const bool ok = gm < M && gk < K;
+                cp_async16(&sm.a[stage][r * (BK + 8) + kc], ok ? A + gm * lda + gk : A, ok);
+            }
+            for (int c = tid; c < BN * (BK / 8); c += kThreads) {
+                const int r = c / (BK / 8), kc = (c % (BK / 8)) * 8;
+                const int gn = n0 + r, gk = kb + kc;
+                const bool ok = gn < N && gk < K;
+                cp_async16(&sm.b[stage][r * (BK + 8) + kc], ok ? B + gn * ldb + gk : B, ok);
+            }
+        } else {
+            // A: BK rows (k) x BM/8 chunks along M
+            for (int c = tid; c < BK * (BM / 8); c += kThreads) {
+                const int r = c / (BM / 8), mc = (c % (BM / 8)) * 8;
+                const int gk = kb + r, gm = m0 + mc;
+                const bool ok = gk < K && gm < M;
+                cp_async16(&sm.a[stage][r * (BM + 8) + mc], ok ? A + gk * lda + gm : A, ok);
+            }
+            for (int c = tid; c < BK * (BN / 8); c += kThreads) {
+                const int r = c / (BN / 8), nc = (c % (BN / 8)) * 8;
+                const int gk = kb + r, gn = n0 + nc;
+                const bool ok = gk < K && gn < N;
+                cp_async16(&sm.b[stage][r * (BN + 8) + nc], ok ? B + gk * ldb + gn : B, ok);
+            }
+        }
+        cp_async_commit();
+    };
+
+    float acc[MI][NI][4];
+#pragma unroll
+    for (int i = 0; i < MI; ++i)
+#pragma unroll
+        for (int j = 0; j < NI; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.0f;
+
+    load_tile(0, ks0);
+    for (int ks = ks0; ks < ks1; ++ks) {
+        const int st = (ks - ks0) & 1;
+        if (ks + 1 < ks1) {
+            load_tile(st ^ 1, ks + 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        const __nv_bfloat16 *as = sm.a[st];
+        const __nv_bfloat16 *bs = sm.b[st];
+#pragma unroll
+        for (int kk = 0; kk < BK; kk += 16) {
+            uint32_t af[MI][4];
+            uint32_t bf[NI][2];
+            const int j = lane >> 3, r = lane & 7;
+#pragma unroll
+            for (int i = 0; i < MI; ++i) {
+                const int mb = wm * TM + i * 16;
+                if (!TRANS) {
+                    const __nv_bfloat16 *p = as + (mb + r + 8 * (j & 1)) * (BK + 8) + kk + 8 * (j >> 1);
+                    ldsm_x4(af[i][0], af[i][1], af[i][2], af[i][3], p);
+                } else {
+                    const __nv_bfloat16 *p = as + (kk + r + 8 * (j >> 1)) * (BM + 8) + mb + 8 * (j & 1);
+                    ldsm_x4_t(af[i][0], af[i][1], af[i][2], af[i][3], p);
+                }
+            }
+#pragma unroll
+            for (int jn = 0; jn < NI; jn += 2) {
+                const int nb = wn * TN + jn * 8;
+                if (!TRANS) {
+                    // matrices: (n 0-7, k 0-7), (n 0-7, k 8-15), (n 8-15, k 0-7), (n 8-15, k 8-15)
+                    const __nv_bfloat16 *p = bs + (nb + r + 8 * (j >> 1)) * (BK + 8) + kk + 8 * (j & 1);
+                    ldsm_x4(bf[jn][0], bf[jn][1], bf[jn + 1][0], bf[jn + 1][1], p);
+                } else {
+                    const __nv_bfloat16 *p = bs + (kk + r + 8 * (j & 1)) * (BN + 8) + nb + 8 * (j >> 1);
+                    ldsm_x4_t(bf[jn][0], bf[jn][1], bf[jn + 1][0], bf[jn + 1][1], p);
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < MI; ++i)
+#pragma unroll
+                for (int jn = 0; jn < NI; ++jn) mma_bf16(acc[i][jn], af[i], bf[jn][0], bf[jn][1]);
+        }
+        __syncthreads();
+    }
+
+    // epilogue: fragment (row = lane/4 [+8], col = 2*(lane%4) + {0,1})
+    const int g = lane >> 2, tg = lane & 3;
+#pragma unroll
+    for (int i = 0; i < MI; ++i)
+#pragma unroll
+        for (int jn = 0; jn < NI; ++jn)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int row = m0 + wm * TM + i * 16 + g + 8 * h;
+                const int col = n0 + wn * TN + jn * 8 + 2 * tg;
+                if (row >= M) continue;
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    if (col + e >= N) continue;
+                    float *dst = C + row * ldc + col + e;
+                    if (TRANS)
+                        atomicAdd(dst, acc[i][jn][2 * h + e]);
+                    else
+                        *dst = acc[i][jn][2 * h + e];
+                }
+            }
+}
+
+}  // namespace gemm
+}  // namespace nsfrb

@@ -584,6 +584,7 @@ void nsfrb_destroy(nsfrb_plan_t plan) {
     cudaFree(plan->d_full_t);
     cudaFree(plan->d_hcube);
     cudaFree(plan->d_hsigma);
+    cudaFree(plan->d_smax_w);
     if (plan->copy_stream) {
         cudaStreamSynchronize(plan->copy_stream);
         cudaStreamDestroy(plan->copy_stream);

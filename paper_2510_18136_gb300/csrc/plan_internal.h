@@ -58,6 +58,9 @@ struct nsfrb_plan_s {
     cudaGraphExec_t s_graph = nullptr;
     cudaEvent_t s_ev_push = nullptr, s_ev_done = nullptr;
     uint32_t *d_mask = nullptr;
+
+    // classifier cutouts: per-DM largest shift and the widths, on the device
+    int32_t *d_smax_w = nullptr;
     int64_t n_pushed = 0;
     bool pending = false;
 };

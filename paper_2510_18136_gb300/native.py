@@ -39,6 +39,13 @@ class nsfrb_candidate(ctypes.Structure):
                 ("t_idx", c_int32), ("snr", c_float)]
 
 
+class nsfrb_clf_config(ctypes.Structure):
+    _fields_ = [("batch", c_int32), ("d", c_int32), ("h", c_int32), ("w", c_int32), ("c0", c_int32),
+                ("c", c_int32 * 4), ("f", c_int32), ("dropout", c_float), ("seed", ctypes.c_uint64),
+                ("lr", c_float), ("beta1", c_float), ("beta2", c_float), ("eps", c_float),
+                ("bn_momentum", c_float)]
+
+
 CANDIDATE_DTYPE = np.dtype([("row", "<i4"), ("col", "<i4"), ("dm_idx", "<i4"), ("w_idx", "<i4"),
                             ("t_idx", "<i4"), ("snr", "<f4")])
 
@@ -72,6 +79,20 @@ def _load() -> ctypes.CDLL:
         "nsfrb_stream_push": ([P, P, c_uint32], c_int32),
         "nsfrb_stream_poll": ([P, c_int32, P, c_int32, POINTER(c_int32), POINTER(c_float)], c_int32),
         "nsfrb_stream_blocks": ([P, POINTER(c_int64)], c_int32),
+        "nsfrb_clf_create": ([POINTER(nsfrb_clf_config), POINTER(c_void_p)], c_int32),
+        "nsfrb_clf_n_params": ([P, POINTER(c_int64)], c_int32),
+        "nsfrb_clf_set_params": ([P, P], c_int32),
+        "nsfrb_clf_get_params": ([P, P], c_int32),
+        "nsfrb_clf_get_grads": ([P, P], c_int32),
+        "nsfrb_clf_get_bn_stats": ([P, P, P], c_int32),
+        "nsfrb_clf_set_bn_stats": ([P, P, P], c_int32),
+        "nsfrb_clf_train_step": ([P, P, P, c_int32, c_int32, POINTER(c_float), P], c_int32),
+        "nsfrb_clf_infer": ([P, P, c_int32, P, P], c_int32),
+        "nsfrb_clf_cutouts": ([P, P, P, P, c_int32, c_int32, c_int32, c_int32, P, P], c_int32),
+        "nsfrb_clf_save": ([P, ctypes.c_char_p], c_int32),
+        "nsfrb_clf_load": ([P, ctypes.c_char_p], c_int32),
+        "nsfrb_clf_destroy": ([P], None),
+        "nsfrb_dbg_gemm": ([c_int32, c_int32, c_int32, c_int32, P, P, P, P], c_int32),
         "nsfrb_destroy": ([P], None),
         "nsfrb_strerror": ([c_int32], ctypes.c_char_p),
         "nsfrb_last_error": ([], ctypes.c_char_p),
@@ -264,3 +285,105 @@ class Plan:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Classifier:
+    """Candidate classifier (``nsfrb_clf_*``): BF16 CNN trained and run by the library's kernels."""
+
+    def __init__(self, batch: int, d: int = 32, h: int = 32, w: int = 32, c0: int = 16,
+                 c=(32, 32, 64, 64), f: int = 32, dropout: float = 0.5, seed: int = 1, lr: float = 1e-3,
+                 beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, bn_momentum: float = 0.1):
+        cfg = nsfrb_clf_config()
+        cfg.batch, cfg.d, cfg.h, cfg.w, cfg.c0 = batch, d, h, w, c0
+        cfg.c = (c_int32 * 4)(*c)
+        cfg.f, cfg.dropout, cfg.seed = f, dropout, seed
+        cfg.lr, cfg.beta1, cfg.beta2, cfg.eps, cfg.bn_momentum = lr, beta1, beta2, eps, bn_momentum
+        self.shape = (d, h, w, c0)
+        self.batch = batch
+        self.n_bn = int(sum(c))
+        hd = c_void_p()
+        _check(lib.nsfrb_clf_create(ctypes.byref(cfg), ctypes.byref(hd)), "nsfrb_clf_create")
+        self._h = hd
+        n = c_int64()
+        _check(lib.nsfrb_clf_n_params(self._h, ctypes.byref(n)), "nsfrb_clf_n_params")
+        self.n_params = int(n.value)
+
+    def set_params(self, p: np.ndarray) -> None:
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == self.n_params
+        _check(lib.nsfrb_clf_set_params(self._h, p.ctypes.data_as(c_void_p)), "nsfrb_clf_set_params")
+
+    def params(self) -> np.ndarray:
+        out = np.empty(self.n_params, dtype=np.float32)
+        _check(lib.nsfrb_clf_get_params(self._h, out.ctypes.data_as(c_void_p)), "nsfrb_clf_get_params")
+        return out
+
+    def grads(self) -> np.ndarray:
+        out = np.empty(self.n_params, dtype=np.float32)
+        _check(lib.nsfrb_clf_get_grads(self._h, out.ctypes.data_as(c_void_p)), "nsfrb_clf_get_grads")
+        return out
+
+    def bn_stats(self):
+        m = np.empty(self.n_bn, dtype=np.float32)
+        v = np.empty(self.n_bn, dtype=np.float32)
+        _check(lib.nsfrb_clf_get_bn_stats(self._h, m.ctypes.data_as(c_void_p), v.ctypes.data_as(c_void_p)),
+               "nsfrb_clf_get_bn_stats")
+        return m, v
+
+    def set_bn_stats(self, m, v) -> None:
+        m = np.ascontiguousarray(m, dtype=np.float32)
+        v = np.ascontiguousarray(v, dtype=np.float32)
+        _check(lib.nsfrb_clf_set_bn_stats(self._h, m.ctypes.data_as(c_void_p), v.ctypes.data_as(c_void_p)),
+               "nsfrb_clf_set_bn_stats")
+
+    def train_step(self, x: torch.Tensor, labels: torch.Tensor, update: bool = True, stream=None,
+                   want_loss: bool = True) -> float | None:
+        """x: [B, d, h, w, c0] bf16 (device); labels [B] float32 (device)."""
+        assert x.is_cuda and x.dtype == torch.bfloat16 and x.is_contiguous() and tuple(x.shape[1:]) == self.shape
+        assert labels.is_cuda and labels.dtype == torch.float32 and labels.numel() == x.shape[0]
+        loss = c_float()
+        _check(lib.nsfrb_clf_train_step(self._h, _ptr(x), _ptr(labels), int(x.shape[0]), int(bool(update)),
+                                        ctypes.byref(loss) if want_loss else None, _stream_handle(stream)),
+               "nsfrb_clf_train_step")
+        return float(loss.value) if want_loss else None
+
+    def infer(self, x: torch.Tensor, stream=None) -> torch.Tensor:
+        """Logits [B] (device float32); p_rfi = sigmoid(logit)."""
+        assert x.is_cuda and x.dtype == torch.bfloat16 and x.is_contiguous() and tuple(x.shape[1:]) == self.shape
+        out = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
+        _check(lib.nsfrb_clf_infer(self._h, _ptr(x), int(x.shape[0]), _ptr(out), _stream_handle(stream)),
+               "nsfrb_clf_infer")
+        return out
+
+    def save(self, path: str) -> None:
+        _check(lib.nsfrb_clf_save(self._h, path.encode()), "nsfrb_clf_save")
+
+    def load(self, path: str) -> None:
+        _check(lib.nsfrb_clf_load(self._h, path.encode()), "nsfrb_clf_load")
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib.nsfrb_clf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cutouts(plan: "Plan", cube: torch.Tensor, cands: torch.Tensor, d: int = 32, h: int = 32, w: int = 32,
+            sigma: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """``nsfrb_clf_cutouts``: cands is a device int32 tensor [n, 6] in nsfrb_candidate layout."""
+    n = int(cands.shape[0])
+    out = torch.empty((n, d, h, w, plan.cfg.n_sub), dtype=torch.bfloat16, device=cube.device)
+    _check(lib.nsfrb_clf_cutouts(plan.handle, _ptr(cube), _ptr(sigma), _ptr(cands), n, d, h, w, _ptr(out),
+                                 _stream_handle(stream)), "nsfrb_clf_cutouts")
+    return out
+
+
+def candidates_to_device(cand: np.ndarray, device="cuda") -> torch.Tensor:
+    """Structured candidate array -> device int32 [n, 6] in nsfrb_candidate layout."""
+    raw = np.ascontiguousarray(cand).view(np.int32).reshape(-1, 6)
+    return torch.from_numpy(raw.copy()).to(device)
