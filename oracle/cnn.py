@@ -41,8 +41,11 @@ def n_params(dims: CnnDims) -> int:
 
 
 def forward_backward(dims: CnnDims, params, x, labels=None, keep=None, p: float = 0.0, train: bool = True,
-                     run_mean=None, run_var=None, grads: bool = True):
-    """x: [B, D, H, W, C0] (channels last). Returns dict(loss, logits, grads, run_mean, run_var)."""
+                     run_mean=None, run_var=None, grads: bool = True, bf16_storage: bool = False):
+    """x: [B, D, H, W, C0] (channels last). Returns dict(loss, logits, grads, run_mean, run_var).
+
+    bf16_storage: round pooled activations and the back-propagated conv-output
+    gradients to bfloat16 where the GPU kernels store them in that format."""
     d = dims.c()
     P = np.ascontiguousarray(params, dtype=np.float64)
     X = np.ascontiguousarray(x, dtype=np.float64)
@@ -54,8 +57,9 @@ def forward_backward(dims: CnnDims, params, x, labels=None, keep=None, p: float 
     rv = np.ones(nc) if run_var is None else np.ascontiguousarray(run_var, dtype=np.float64).copy()
     logits = np.empty(dims.B)
     G = np.empty_like(P) if (grads and train and L is not None) else None
-    loss = _load().orc_cnn_forward_backward(ctypes.byref(d), _p(P), _p(X), _p(L), _p(K), float(p),
-                                            int(bool(train)), _p(rm), _p(rv), _p(logits), _p(G))
+    loss = _load().orc_cnn_forward_backward_ex(ctypes.byref(d), _p(P), _p(X), _p(L), _p(K), float(p),
+                                               int(bool(train)), _p(rm), _p(rv), _p(logits), _p(G),
+                                               int(bool(bf16_storage)))
     return {"loss": loss, "logits": logits, "grads": G, "run_mean": rm, "run_var": rv}
 
 
@@ -95,4 +99,33 @@ def layout(dims: CnnDims):
     for name, shape in [("fc1.w", (dims.F, fin)), ("fc1.b", (dims.F,)), ("fc2.w", (dims.F,)), ("fc2.b", (1,))]:
         out.append((name, o, shape))
         o += int(np.prod(shape))
+    return out
+
+
+def cutouts_grid(cube, ny, nx, cands, smax, widths, D, H, W, sigma=None):
+    """As ``cutouts`` with the image shape given explicitly."""
+    n_pix, n_sub, n_t = cube.shape
+    out = np.zeros((len(cands), D, H, W, n_sub))
+    for i, c in enumerate(cands):
+        w = int(widths[int(c["w_idx"])])
+        sm = int(smax[int(c["dm_idx"])])
+        span = w + sm
+        b = max(1, -(-span // (D // 2)))
+        ts = int(c["t_idx"]) + span // 2 - (D * b) // 2
+        pc = int(c["row"]) * nx + int(c["col"])
+        sg = 1.0 if sigma is None else float(sigma[pc]) / np.sqrt(n_sub)
+        for y in range(H):
+            r = int(c["row"]) - H // 2 + y
+            if r < 0 or r >= ny:
+                continue
+            for x in range(W):
+                cc = int(c["col"]) - W // 2 + x
+                if cc < 0 or cc >= nx:
+                    continue
+                p = r * nx + cc
+                for z in range(D):
+                    t0 = ts + z * b
+                    lo, hi = max(t0, 0), min(t0 + b, n_t)
+                    s = cube[p, :, lo:hi].astype(np.float64).sum(axis=1) if hi > lo else np.zeros(n_sub)
+                    out[i, z, y, x, :] = s / b / sg
     return out

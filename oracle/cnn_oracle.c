@@ -121,6 +121,21 @@ static void conv3d(int B, int D, int H, int W, int cin, int cout, const double *
 
 /* ----------------------------------------------------------- forward / backward */
 
+/* Round to bfloat16 (nearest, ties to even) and back: the storage format in
+ * which the GPU kernels keep pooled activations and back-propagated conv
+ * gradients.  With bf16_storage set, the oracle rounds at exactly those
+ * places, so that max-pool arg-max decisions are taken on the same values. */
+static double round_bf16(double v)
+{
+    float f = (float)v;
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    u &= 0xFFFF0000u;
+    memcpy(&f, &u, 4);
+    return (double)f;
+}
+
 /*
  * Forward and (if grads != NULL) backward of the mean BCE loss.
  *   x[B][D][H][W][C0], labels[B] in {0, 1} (1 = artefact / RFI),
@@ -131,9 +146,10 @@ static void conv3d(int B, int D, int H, int W, int cin, int cout, const double *
  *   the batch mean and the unbiased batch variance are returned in them.
  * logits[B] receive the outputs; returns the loss (0 if labels == NULL).
  */
-double orc_cnn_forward_backward(const orc_cnn_dims *d, const double *params, const double *x,
-                                const double *labels, const uint8_t *keep, double p, int train,
-                                double *run_mean, double *run_var, double *logits, double *grads)
+double orc_cnn_forward_backward_ex(const orc_cnn_dims *d, const double *params, const double *x,
+                                   const double *labels, const uint8_t *keep, double p, int train,
+                                   double *run_mean, double *run_var, double *logits, double *grads,
+                                   int bf16_storage)
 {
     const int B = d->B;
     int dims[5][4];   /* per stage: D, H, W, C of the activation entering conv l (stage 4 = pooled output) */
@@ -220,7 +236,8 @@ double orc_cnn_forward_backward(const orc_cnn_dims *d, const double *params, con
                                         if (v < 0.0) v = 0.0;
                                         if (v > m) m = v;
                                     }
-                            act[l + 1][((((int64_t)b * D2 + z) * H2 + y) * W2 + xw) * cout + c] = m;
+                            act[l + 1][((((int64_t)b * D2 + z) * H2 + y) * W2 + xw) * cout + c] =
+                                bf16_storage ? round_bf16(m) : m;
                         }
         rs_off += cout;
     }
@@ -308,9 +325,10 @@ double orc_cnn_forward_backward(const orc_cnn_dims *d, const double *params, con
                 grads[off_b[l] + c] = sdz;
                 grads[off_g[l] + c] = sdzh;
                 const double N = (double)npos[l];
-                for (int64_t q = 0; q < npos[l]; ++q)
-                    dy[q * cout + c] = g[c] * rstd[l][c] / N *
-                                       (N * dz[q * cout + c] - sdz - yhat[l][q * cout + c] * sdzh);
+                for (int64_t q = 0; q < npos[l]; ++q) {
+                    double v = g[c] * rstd[l][c] / N * (N * dz[q * cout + c] - sdz - yhat[l][q * cout + c] * sdzh);
+                    dy[q * cout + c] = bf16_storage ? round_bf16(v) : v;
+                }
             }
             /* conv backward: weights and input */
             double *dw = grads + off_w[l];
@@ -351,6 +369,13 @@ double orc_cnn_forward_backward(const orc_cnn_dims *d, const double *params, con
     free(h1);
     free(h1d);
     return loss;
+}
+
+double orc_cnn_forward_backward(const orc_cnn_dims *d, const double *params, const double *x,
+                                const double *labels, const uint8_t *keep, double p, int train,
+                                double *run_mean, double *run_var, double *logits, double *grads)
+{
+    return orc_cnn_forward_backward_ex(d, params, x, labels, keep, p, train, run_mean, run_var, logits, grads, 0);
 }
 
 /* One Adam step (Kingma & Ba 2015) on n parameters, step t >= 1:

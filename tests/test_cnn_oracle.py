@@ -141,3 +141,42 @@ def test_adam_matches_torch():
         tp.grad = torch.tensor(g)
         opt.step()
     np.testing.assert_allclose(p, tp.detach().numpy(), rtol=1e-12, atol=1e-14)
+
+
+def test_cutout_hand_example():
+    """One bright sample: cube 6x5 px, 2 subbands, 40 samples; candidate at (row 3, col 1),
+    width 2, largest shift 2 -> span 4, bin b = 1 for D = 16 (span <= 8), window start
+    ts = t_idx + 2 - 8.  With t_idx = 20: ts = 14, so sample t = 21 of subband 1 at pixel
+    (2, 2) lands at z = 7, y = 2 - 3 + 8 = 7, x = 2 - 1 + 8 = 9."""
+    cube = np.zeros((30, 2, 40))
+    cube[2 * 5 + 2, 1, 21] = 8.0
+    cands = np.zeros(1, dtype=[("row", "<i4"), ("col", "<i4"), ("dm_idx", "<i4"), ("w_idx", "<i4"),
+                               ("t_idx", "<i4"), ("snr", "<f4")])
+    cands[0] = (3, 1, 0, 0, 20, 9.0)
+    out = cnn.cutouts_grid(cube, 6, 5, cands, smax=np.array([2]), widths=np.array([2]), D=16, H=16, W=16,
+                           sigma=np.full(30, 2.0 * np.sqrt(2.0)))
+    assert out.shape == (1, 16, 16, 16, 2)
+    nz = np.argwhere(out != 0)
+    assert nz.tolist() == [[0, 7, 7, 9, 1]]
+    assert out[0, 7, 7, 9, 1] == 8.0 / 2.0
+    # a wide pulse: width 64, shift 0 -> span 64, b = 8, window start 20 + 32 - 64 = -12;
+    # bin z averages samples -12 + 8z .. -5 + 8z, so sample 21 falls in z = 4
+    cube2 = np.zeros((30, 2, 40))
+    cube2[3 * 5 + 1, 0, 21] = 8.0
+    out2 = cnn.cutouts_grid(cube2, 6, 5, cands, smax=np.array([0]), widths=np.array([64]), D=16, H=16, W=16)
+    assert np.argwhere(out2 != 0).tolist() == [[0, 4, 8, 8, 0]]
+    assert out2[0, 4, 8, 8, 0] == 1.0
+
+
+def test_bf16_storage_mode_rounds_only_storage():
+    """bf16_storage changes results by about the bfloat16 unit roundoff, no more."""
+    rng = np.random.default_rng(21)
+    x = rng.standard_normal((DIMS.B, DIMS.D, DIMS.H, DIMS.W, DIMS.C0))
+    labels = np.array([1.0, 0.0, 1.0])
+    params = _params(DIMS, 6)
+    a = cnn.forward_backward(DIMS, params, x, labels)
+    b = cnn.forward_backward(DIMS, params, x, labels, bf16_storage=True)
+    assert b["loss"] == pytest.approx(a["loss"], rel=2e-2)
+    assert b["loss"] != a["loss"]
+    rounded = torch.tensor(b["logits"], dtype=torch.float32)
+    assert torch.isfinite(rounded).all()
