@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving-blocks", type=int, default=40,
                     help="blocks per field of the 4-field serving latency run (0: skip)")
+    ap.add_argument("--classifier-samples", type=int, default=6000,
+                    help="labelled cutouts for the classifier section (0: skip)")
+    ap.add_argument("--classifier-epochs", type=int, default=2)
     ap.add_argument("--seed", type=int, default=0)
     return ap.parse_args()
 
@@ -274,6 +277,68 @@ def serving_latency(native, synth, n_blocks: int, seed: int = 0):
             "cadence_s": 3.355}
 
 
+# ----------------------------------------------------------------------------- classifier
+
+def clf_flops_per_sample(d=32, h=32, w=32, c0=16, c=(32, 32, 64, 64)):
+    """Algorithmic FLOPs of the four conv blocks per cutout: forward 2 P Co 27 Ci per block;
+    training adds the weight gradient (same) and the input gradient (same, blocks 1-3)."""
+    fwd, dx = 0.0, 0.0
+    cin, dd, hh, ww = c0, d, h, w
+    for l, co in enumerate(c):
+        f = 2.0 * dd * hh * ww * co * 27 * cin
+        fwd += f
+        if l > 0:
+            dx += f
+        cin, dd, hh, ww = co, dd // 2, hh // 2, ww // 2
+    return fwd, 2 * fwd + dx
+
+
+def classifier_section(native, n_samples: int, epochs: int, seed: int = 0):
+    """Train the candidate classifier on search-produced cutouts; report rates and throughput."""
+    import torch
+    from paper_2510_18136_gb300 import clfdata
+    cfg = clfdata.search_config()
+    t0 = time.perf_counter()
+    x, y, _ = clfdata.dataset(n_samples, seed=100 + seed)
+    t_data = time.perf_counter() - t0
+    clf = native.Classifier(batch=64, dropout=0.5, seed=7 + seed, lr=1e-3)
+    clfdata.init_params(clf, seed=3 + seed)
+    clfdata.train(clf, x, y, epochs=1, seed=seed)          # warm-up epoch
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    losses = clfdata.train(clf, x, y, epochs=epochs, seed=seed + 1)
+    e1.record()
+    torch.cuda.synchronize()
+    t_train = e0.elapsed_time(e1) / 1e3
+    n_seen = epochs * (x.shape[0] // clf.batch) * clf.batch
+    i0, i1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    xb = x[:clf.batch].contiguous()
+    clf.infer(xb)
+    i0.record()
+    for _ in range(20):
+        clf.infer(xb)
+    i1.record()
+    torch.cuda.synchronize()
+    t_inf = i0.elapsed_time(i1) / 1e3
+    ev = clfdata.evaluate(clf, cfg, range(9000 + 100 * seed, 9012 + 100 * seed))
+    thr = clfdata.rates(ev["label"], ev["detected"])
+    c15 = clfdata.rates(ev["label"], ev["detected"], ev["p_rfi"], 0.15)
+    c50 = clfdata.rates(ev["label"], ev["detected"], ev["p_rfi"], 0.5)
+    fwd, train_f = clf_flops_per_sample()
+    pk = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"bf16_tflops": 1900.0}
+    train_tflops = n_seen * train_f / t_train / 1e12
+    clf.close()
+    return {"cutout": "32x32 px x 16 subbands x 32 samples (bf16)", "net": "4 conv (16-32-32-64-64) + FC 32 + FC 1",
+            "train_samples": int(x.shape[0]), "epochs_timed": epochs, "final_loss": losses[-1],
+            "train_samples_per_s": n_seen / t_train, "train_conv_tflops": train_tflops,
+            "train_tensor_frac_of_bf16_peak": train_tflops / float(pk["bf16_tflops"]),
+            "infer_cutouts_per_s": 20 * clf.batch / t_inf, "data_gen_s": t_data,
+            "threshold_only": thr, "with_classifier_p_lt_0.15": c15, "with_classifier_p_lt_0.5": c50,
+            "threshold_method": "GPU search (parity with the FP64 oracle is a test)"}
+
+
 # ----------------------------------------------------------------------------- GPU arm
 
 def main():
@@ -357,6 +422,9 @@ def main():
     serving = None
     if args.serving_blocks > 0 and rank == 0:
         serving = serving_latency(native, synth, args.serving_blocks, seed=args.seed)
+    classifier = None
+    if args.classifier_samples > 0 and rank == 0:
+        classifier = classifier_section(native, args.classifier_samples, args.classifier_epochs, seed=args.seed)
 
     pk = peaks()
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -387,6 +455,7 @@ def main():
         "candidates": int(len(cand)), "injections": int(len(inj)),
         "p99_block_latency_ms": None if serving is None else serving["p99_ms"],
         "serving": serving,
+        "classifier": classifier,
         "clocks": ck,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
