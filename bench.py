@@ -90,7 +90,7 @@ def make_cube(native, synth, cfg, seed, device, dtype):
 
 # DRAM bytes (read + write) per 301x301 FP32 launch from the ncu capture summarised in
 # profiles/search_kernel_full_window.md, valid for the kernel source with this sha256 prefix.
-NCU_TRAFFIC = {"sha256_16": "591f2879b6f4752f", "bytes": 7.034e9, "workload": (301, 301, "f32")}
+NCU_TRAFFIC = {"sha256_16": "d2a2366b1a982ccb", "bytes": 7.034e9, "workload": (301, 301, "f32")}
 
 
 def measured_traffic(ny, nx, dtype):

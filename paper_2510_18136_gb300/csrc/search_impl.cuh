@@ -3,13 +3,13 @@
 // every width with prefix sums, normalise to S/N, maximise over time, width
 // and DM.  Included by one translation unit per chunk size C.
 //
-// Organisation (one CTA of 8 warps per pixel, persistent over pixels):
+// Organisation (one CTA of 12 warps per pixel, persistent over pixels):
 //  * The pixel's [n_sub][n_t] tile is staged in shared memory (bulk copies
 //    into a double buffer for FP32, or into a 16-bit staging double buffer
 //    that is widened to FP32), with -inf beyond n_t so that every time series
 //    element that would read past the window is non-finite.
 //  * Distinct shift rows (DM trials with identical integer tables are one
-//    row) are split into 8 contiguous groups, one per warp.  A warp builds
+//    row) are split into 12 contiguous groups, one per warp.  A warp builds
 //    the first row of its group from all subbands and each later row from
 //    the previous one by adding/subtracting only the subbands whose shift
 //    changed (sorted DMs change a few subbands per row).
