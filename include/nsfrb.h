@@ -153,6 +153,49 @@ nsfrb_status nsfrb_full(nsfrb_plan_t plan, float *out_snr, int16_t *out_t_idx);
  * waits for the search.  ENOTREADY before the first search. */
 nsfrb_status nsfrb_last_timing(nsfrb_plan_t plan, float *search_ms, float *total_ms);
 
+/* ---- longer timescales (Sec. 2.2: the search is repeated on data binned by 5
+ * samples (0.67 s, DM range x5 so that the same integer shifts apply) and by
+ * 75 samples (10.05 s, no de-dispersion)) --------------------------------
+ * d_out[r][j] = sum_{q < factor} d_in[r][j*factor + q] for every row r of
+ * n_t samples (a (pixel, subband) row of a pixel-major cube: n_rows =
+ * ny*nx*n_sub), j < n_t / factor; a trailing remainder is dropped.  d_in in
+ * `dtype` storage, d_out FP32; device pointers; asynchronous.  The noise of a
+ * binned sample is sqrt(factor) times the unbinned one: search the binned cube
+ * with sigma_D scaled by sqrt(factor) (KNOWN mode).  EINVAL on bad sizes. */
+nsfrb_status nsfrb_bin_time(const void *d_in, int32_t dtype, int64_t n_rows, int32_t n_t, int32_t factor,
+                            float *d_out, void *stream);
+
+/* ---- PSF-based candidate clustering (Sec. 2.3: the top candidates by S/N
+ * are compared with the point-spread function; the PSF thresholded at its
+ * 90th percentile is a binary mask centred on each candidate in turn, the
+ * other candidates inside it are possible sidelobes, a weighted mean S/N is
+ * formed over the central and sidelobe candidates, and the central candidate
+ * of the largest one is the final, most likely candidate) ----------------- */
+typedef struct {
+    nsfrb_candidate final_cand;   /* central candidate of the best cluster      */
+    float weighted_snr;           /* its PSF-weighted mean S/N                    */
+    int32_t n_top;                /* candidates considered (min(top_k, n))        */
+    int32_t final_rank;           /* index of final_cand in the top list, or -1   */
+    uint32_t members;             /* bit j set: top candidate j is in its cluster */
+} nsfrb_cluster_result;
+
+/* d_cand[n]: candidates (device, e.g. a copy of nsfrb_candidates' output);
+ * nx: image width (pixel index = row*nx + col, used only to order equal S/N);
+ * d_psf[ph][pw]: PSF image (device FP32, peak at (ph/2, pw/2)), ph*pw <= 4096;
+ * percentile: mask threshold (90 in the paper; linear interpolation between
+ * order statistics); top_k (10 in the paper, <= 32).
+ * Outputs (device): d_top[min(top_k, n)] the top candidates by S/N (ties:
+ * smaller pixel index first) and one nsfrb_cluster_result at d_result.
+ * Score of a cluster: the mean of the members' S/N referred to the central
+ * lobe (snr_j / psf_j, psf_j the PSF value at member j's offset from the
+ * central candidate) with inverse-variance weights psf_j^2, i.e.
+ * sum_j psf_j snr_j / sum_j psf_j^2 (the least-squares source S/N under the
+ * PSF template); for a peak-normalised PSF the central candidate enters with
+ * psf = 1.  Asynchronous. */
+nsfrb_status nsfrb_psf_cluster(const nsfrb_candidate *d_cand, int32_t n, int32_t nx, const float *d_psf,
+                               int32_t ph, int32_t pw, float percentile, int32_t top_k, nsfrb_candidate *d_top,
+                               void *d_result, void *stream);
+
 /* ---- search without device allocation -------------------------------------
  * The paper has no counterpart to this call.  It serves callers that cannot
  * allocate device memory at search time: code that runs while another

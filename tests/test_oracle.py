@@ -280,3 +280,20 @@ def test_bf16_rounding_matches_torch():
     a = (rng.standard_normal(10000) * 10).astype(np.float32)
     ref = torch.from_numpy(a).to(torch.bfloat16).to(torch.float32).numpy()
     np.testing.assert_array_equal(oracle.bf16_round(a), ref)
+
+
+def test_psf_cluster_hand_example():
+    """3x3 PSF [[.1,.5,.1],[.5,1,.5],[.1,.5,.1]], 50th percentile -> mask = centre + 4 neighbours.
+    A (5,5) 10, B (5,6) 9, C (6,5) 8, D (9,9) 9.5; score = sum psf*snr / sum psf^2 over members:
+    A: (10 + 4.5 + 4)/(1 + .25 + .25) = 12.33;  B: (9 + 5)/1.25 = 11.2;  C: (8 + 5)/1.25 = 10.4;
+    D: 9.5.  A, whose neighbours look like its PSF response, is the final candidate."""
+    from oracle import postproc
+    c = np.zeros(4, dtype=[("row", "<i4"), ("col", "<i4"), ("dm_idx", "<i4"), ("w_idx", "<i4"),
+                           ("t_idx", "<i4"), ("snr", "<f4")])
+    c["row"], c["col"], c["snr"] = [5, 5, 6, 9], [5, 6, 5, 9], [10.0, 9.0, 8.0, 9.5]
+    psf = np.array([[0.1, 0.5, 0.1], [0.5, 1.0, 0.5], [0.1, 0.5, 0.1]])
+    top, best, score, mask = postproc.psf_cluster(c, 16, psf, percentile=50.0, top_k=10)
+    assert list(top["snr"]) == [10.0, 9.5, 9.0, 8.0]
+    assert (int(top["row"][best]), int(top["col"][best])) == (5, 5)
+    assert score == pytest.approx(18.5 / 1.5)
+    assert mask == 0b1101   # top order: A (10), D (9.5), B (9), C (8); members A, B, C
