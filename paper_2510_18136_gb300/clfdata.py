@@ -64,10 +64,10 @@ def _shifts(plan_cache, cfg, dms):
     return out
 
 
-def make_cube(cfg: synth.SearchConfig, seed: int, device="cuda", snr=(6.0, 30.0), spacing: int = 32):
-    """One cube with sources on a jittered grid (one source per spacing x spacing cell).
-
-    Returns (cube FP32 [n_pix, n_sub, n_t] on device, Truth)."""
+def make_cube(cfg: synth.SearchConfig, seed: int, device="cuda", snr=(6.0, 30.0), spacing: int = 32,
+              kinds_allowed=(KIND_BURST, KIND_BURST, KIND_BRIGHT, KIND_STEP, KIND_SPIKE)):
+    """One cube with sources on a jittered grid (one source per spacing x spacing cell), each of a
+    kind drawn from kinds_allowed.  Returns (cube FP32 [n_pix, n_sub, n_t] on device, Truth)."""
     rng = np.random.default_rng(seed)
     cube = synth.psf_noise(cfg, seed, device=device)
     sig_pix = synth.psf_sigma()
@@ -77,7 +77,7 @@ def make_cube(cfg: synth.SearchConfig, seed: int, device="cuda", snr=(6.0, 30.0)
     rng.shuffle(cells)
     kinds, rows, cols, t0s, ws, dms, snrs = [], [], [], [], [], [], []
     for (r0, c0) in cells:
-        kind = int(rng.choice([KIND_BURST, KIND_BURST, KIND_BRIGHT, KIND_STEP, KIND_SPIKE]))
+        kind = int(rng.choice(list(kinds_allowed)))
         r = r0 + int(rng.integers(-3, 4))
         c = c0 + int(rng.integers(-3, 4))
         if kind == KIND_BRIGHT:
