@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--classifier-samples", type=int, default=6000,
                     help="labelled cutouts for the classifier section (0: skip)")
     ap.add_argument("--classifier-epochs", type=int, default=2)
+    ap.add_argument("--imager-steps", type=int, default=20,
+                    help="timed launches of the imager section, one 25-sample block each (0: skip)")
     ap.add_argument("--seed", type=int, default=0)
     return ap.parse_args()
 
@@ -339,6 +341,65 @@ def classifier_section(native, n_samples: int, epochs: int, seed: int = 0):
             "threshold_method": "GPU search (parity with the FP64 oracle is a test)"}
 
 
+# ----------------------------------------------------------------------------- imager
+
+def imager_section(native, steps: int, seed: int = 0):
+    """Image one 25-sample block (16 subbands x 8 channels, 82-antenna core, 175 px, R = -2) per
+    launch; HBM roofline on the visibilities read and images written; the FP64 oracle timed on
+    a few images of the same block."""
+    import torch
+    from oracle import imager as oi
+    from paper_2510_18136_gb300 import synth_vis as sv
+    n_t, N, pix = 25, 175, 10.3
+    ant = sv.core_layout(seed)
+    uv = sv.baseline_uv(ant)
+    chan = sv.channel_freqs()
+    n_sub, n_chan = chan.shape
+    vis = sv.visibilities(uv, chan, n_t, [(12, -7, 5.0)], pixel_arcsec=pix, noise=1.0, seed=seed, device="cuda")
+    vis_f = torch.view_as_real(vis).contiguous()
+    im = native.Imager(uv, chan, n_grid=N, pixel_arcsec=pix)
+    u_max, v_max, n_entries = im.info()
+    out = torch.empty((n_t, n_sub, N, N), dtype=torch.float32, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        im.image(vis_f, out=out, stream=stream)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        im.image(vis_f, out=out, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    t = statistics.median(times)
+    vis_bytes = vis_f.numel() * 4
+    img_bytes = out.numel() * 4
+    alg = vis_bytes + img_bytes + 8 * n_entries
+    pk = peaks()
+    # oracle on a few images of the same block
+    vh = vis.cpu().numpy()
+    pairs = [(0, 0), (12, 7), (24, 15)]
+    c0 = time.perf_counter()
+    for tt, ss in pairs:
+        oi.image(vh[tt:tt + 1, ss:ss + 1], uv, chan[ss:ss + 1], N, pix)
+    t_cpu = (time.perf_counter() - c0) / len(pairs)
+    im.close()
+    return {"workload": f"{n_t} samples x {n_sub} subbands x {n_chan} channels x {len(uv)} baselines x 2 pol "
+                        f"-> {n_t * n_sub} images {N}x{N} (10.3 arcsec, Briggs R=-2, b 20-485 m)",
+            "uv_support": [u_max, v_max], "gridding_entries": n_entries,
+            "ms_per_block": t * 1e3, "images_per_s": n_t * n_sub / t,
+            "visibilities_per_s": n_t * n_sub * n_chan * len(uv) * 2 / t,
+            "roofline": {"bound": "hbm", "achieved": alg / t / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                         "frac": alg / t / 1e9 / pk["hbm_gbs"], "bytes_per_launch": alg, "kernel": "image_kernel",
+                         "traffic": None},
+            "l2": "256 MB buffer written between launches",
+            "cpu_baseline": {"value": 1.0 / t_cpu, "unit": "images/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{len(pairs)} images of the block, FP64 numpy"}}
+
+
 # ----------------------------------------------------------------------------- GPU arm
 
 def main():
@@ -426,6 +487,10 @@ def main():
     if args.classifier_samples > 0 and rank == 0:
         classifier = classifier_section(native, args.classifier_samples, args.classifier_epochs, seed=args.seed)
 
+    imager = None
+    if args.imager_steps > 0 and rank == 0:
+        imager = imager_section(native, args.imager_steps, seed=args.seed)
+
     pk = peaks()
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     kern_s = statistics.mean(search_ms) / 1e3
@@ -456,6 +521,7 @@ def main():
         "p99_block_latency_ms": None if serving is None else serving["p99_ms"],
         "serving": serving,
         "classifier": classifier,
+        "imager": imager,
         "clocks": ck,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

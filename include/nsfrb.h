@@ -260,6 +260,67 @@ nsfrb_status nsfrb_stream_poll(nsfrb_plan_t plan, int32_t timeout_ms, nsfrb_cand
  * partly empty: their missing samples are zero). */
 nsfrb_status nsfrb_stream_blocks(nsfrb_plan_t plan, int64_t *n_blocks);
 
+/* Device-resident blocks, for an imager on the same GPU (Sec. 2.1 images
+ * feeding the Sec. 2.2 search without a host round trip).
+ * nsfrb_stream_block: *d_block = the stream's block buffer, device FP32
+ * [n_blk][n_sub][ny][nx], owned by the plan (valid until nsfrb_destroy).
+ * Write the next block there only after the previous block has been polled.
+ * nsfrb_stream_push_device: queue the block already in that buffer; the
+ * search waits for the work queued so far on `stream` (the producer's
+ * stream; NULL = legacy default stream).  Otherwise as nsfrb_stream_push. */
+nsfrb_status nsfrb_stream_block(nsfrb_plan_t plan, float **d_block);
+nsfrb_status nsfrb_stream_push_device(nsfrb_plan_t plan, uint32_t present_mask, void *stream);
+
+/* ---- imager (Sec. 2.1, fringe-stopping and imaging: core baselines longer
+ * than b_min, polarisations summed, Briggs weighting with robustness R on an
+ * N x N uv-grid, 2-D inverse FFT with the grid and the image shifted by
+ * ifftshift; each channel imaged separately and the channel images summed
+ * into one image per subband and 134 ms sample) ----------------------------
+ * Definitions (u, v in metres, f the channel frequency, dtheta the pixel):
+ *   a baseline is kept when b_min < sqrt(u^2 + v^2) < b_max;
+ *   its cell is k = rint(u * f_MHz * 1e6 / c * N * dtheta) per axis (FP64,
+ *   left to right, ties to even), its conjugate goes to -k; cells with
+ *   |k| > (N - 1) / 2 are dropped with their mirror;
+ *   per channel, W_cell counts the visibilities in each cell (mirrors
+ *   included), f^2 = (5 * 10^-R)^2 / (sum_cells W^2 / sum w) and each
+ *   visibility is weighted 1 / (1 + W_cell f^2);
+ *   image[y][x] = Re sum_k G_k exp(2 pi i (ku (x + N/2) + kv (y + N/2)) / N) / N^2
+ *   (integer N/2), summed over the subband's channels: numpy's
+ *   ifftshift(ifft2(ifftshift(G))).real with the zero frequency at N/2. */
+typedef struct nsfrb_imager_s *nsfrb_imager_t;
+typedef struct {
+    int32_t n_grid;           /* N, uv-grid and image side: 175 in Sec. 2.1; 3..1024        */
+    double pixel_arcsec;      /* image pixel: 10.3 arcsec in Sec. 2.1                          */
+    double robust;            /* Briggs robustness R: -2 in Sec. 2.1                           */
+    double b_min_m, b_max_m;  /* kept baselines: b_min < |b| < b_max (20 m, 485 m)             */
+    int32_t n_base;           /* baselines                                                     */
+    const double *uv_m;       /* [n_base][2] (u, v) in metres, host, copied                    */
+    int32_t n_sub, n_chan;    /* subbands (16) and channels per subband (8)                    */
+    const double *chan_mhz;   /* [n_sub][n_chan] channel centres in MHz, host, copied          */
+} nsfrb_imager_config;
+
+/* Plan the imager on the current device: selection, cells and weights in
+ * FP64 on the host, gridding tables and twiddles on the device.  EINVAL on a
+ * bad configuration or a uv support too large for one CTA's shared memory;
+ * ENOMEM / ECUDA from the device. */
+nsfrb_status nsfrb_imager_create(const nsfrb_imager_config *cfg, nsfrb_imager_t *out);
+
+/* h_w[n_sub][n_chan][n_base] (host): the Briggs weight of every baseline at
+ * every channel, 0 where the baseline is dropped. */
+nsfrb_status nsfrb_imager_weights(nsfrb_imager_t im, float *h_w);
+
+/* Extent of the occupied half-plane uv support (0 <= ku <= u_max,
+ * |kv| <= v_max) and the number of gridding entries; any pointer may be NULL. */
+nsfrb_status nsfrb_imager_info(nsfrb_imager_t im, int32_t *u_max, int32_t *v_max, int64_t *n_entries);
+
+/* d_vis: device FP32 [n_t][n_sub][n_chan][n_base][2 pol][re, im], 16-byte
+ * aligned.  d_img: device FP32 [n_t][n_sub][N][N] (the serving block layout
+ * when N x N is the search plan's ny x nx).  Asynchronous on `stream`.
+ * Accumulates in FP32 (gridding in a fixed order: results are reproducible
+ * bit for bit). */
+nsfrb_status nsfrb_image(nsfrb_imager_t im, const float *d_vis, int32_t n_t, float *d_img, void *stream);
+void nsfrb_imager_destroy(nsfrb_imager_t im);
+
 /* ---- candidate classifier (Sec. 2.3: convolutional blocks with batch
  * normalisation, a non-linearity and max-pooling, a small fully connected
  * head with dropout, one logit per candidate interpreted through a sigmoid as

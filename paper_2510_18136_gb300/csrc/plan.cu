@@ -109,7 +109,10 @@ bool choose_stage(const nsfrb_plan_s *pl, SearchParams &sp, size_t &smem) {
     const int n_t = sp.n_t;
     int want = 0;
     if (sp.dtype == NSFRB_F32) {
-        if (base % 16 == 0 && n_t % 4 == 0 && sp.row_len % 4 == 0 && sp.t_off % 4 == 0) want = 1;
+        // bulk copies start at the window start: 16-byte aligned only if it is a multiple of 4
+        // samples.  A window start kept on the device (serving) moves by new_blk per block.
+        const bool start_aligned = sp.t_off_dev ? (sp.new_blk > 0 && sp.new_blk % 4 == 0) : (sp.t_off % 4 == 0);
+        if (base % 16 == 0 && n_t % 4 == 0 && sp.row_len % 4 == 0 && start_aligned) want = 1;
     } else {
         if (base % 16 == 0 && sp.row_len % 8 == 0 &&
             (sp.t_off_dev ? sp.row_len >= 2 * static_cast<int64_t>(n_t) + 8 : sp.t_off + n_t <= sp.row_len))

@@ -229,6 +229,32 @@ nsfrb_status nsfrb_stream_push(nsfrb_plan_t plan, const float *h_block, uint32_t
     return NSFRB_OK;
 }
 
+nsfrb_status nsfrb_stream_block(nsfrb_plan_t plan, float **d_block) {
+    if (!plan || !d_block) return fail(plan, NSFRB_EINVAL, "null argument");
+    if (!plan->streaming) return fail(plan, NSFRB_EINVAL, "stream not open");
+    *d_block = plan->d_blk;
+    return NSFRB_OK;
+}
+
+nsfrb_status nsfrb_stream_push_device(nsfrb_plan_t plan, uint32_t present_mask, void *stream) {
+    if (!plan) return fail(plan, NSFRB_EINVAL, "null argument");
+    if (!plan->streaming) return fail(plan, NSFRB_EINVAL, "stream not open");
+    if (plan->pending) return fail(plan, NSFRB_ENOTREADY, "previous block not polled");
+    cudaStream_t s = plan->s_stream;
+    const uint32_t m = present_mask;
+    nsfrb_status st;
+    // the producer's work on `stream` (the block written into d_blk) comes first
+    if ((st = cuda_check(plan, cudaEventRecord(plan->s_ev_push, static_cast<cudaStream_t>(stream)), "event")) ||
+        (st = cuda_check(plan, cudaStreamWaitEvent(s, plan->s_ev_push, 0), "wait")) ||
+        (st = cuda_check(plan, cudaMemcpyAsync(plan->d_mask, &m, sizeof(m), cudaMemcpyHostToDevice, s), "mask")) ||
+        (st = cuda_check(plan, cudaGraphLaunch(plan->s_graph, s), "graph launch")) ||
+        (st = cuda_check(plan, cudaEventRecord(plan->s_ev_done, s), "event")))
+        return st;
+    plan->pending = true;
+    ++plan->n_pushed;
+    return NSFRB_OK;
+}
+
 nsfrb_status nsfrb_stream_poll(nsfrb_plan_t plan, int32_t timeout_ms, nsfrb_candidate *h_out, int32_t cap,
                                int32_t *n_total, float *latency_ms) {
     if (!plan || !n_total || cap < 0 || (cap > 0 && !h_out)) return fail(plan, NSFRB_EINVAL, "bad argument");

@@ -46,6 +46,12 @@ class nsfrb_clf_config(ctypes.Structure):
                 ("bn_momentum", c_float)]
 
 
+class nsfrb_imager_config(ctypes.Structure):
+    _fields_ = [("n_grid", c_int32), ("pixel_arcsec", c_double), ("robust", c_double), ("b_min_m", c_double),
+                ("b_max_m", c_double), ("n_base", c_int32), ("uv_m", POINTER(c_double)), ("n_sub", c_int32),
+                ("n_chan", c_int32), ("chan_mhz", POINTER(c_double))]
+
+
 CANDIDATE_DTYPE = np.dtype([("row", "<i4"), ("col", "<i4"), ("dm_idx", "<i4"), ("w_idx", "<i4"),
                             ("t_idx", "<i4"), ("snr", "<f4")])
 
@@ -79,6 +85,13 @@ def _load() -> ctypes.CDLL:
         "nsfrb_stream_push": ([P, P, c_uint32], c_int32),
         "nsfrb_stream_poll": ([P, c_int32, P, c_int32, POINTER(c_int32), POINTER(c_float)], c_int32),
         "nsfrb_stream_blocks": ([P, POINTER(c_int64)], c_int32),
+        "nsfrb_stream_block": ([P, POINTER(c_void_p)], c_int32),
+        "nsfrb_stream_push_device": ([P, c_uint32, P], c_int32),
+        "nsfrb_imager_create": ([POINTER(nsfrb_imager_config), POINTER(c_void_p)], c_int32),
+        "nsfrb_imager_weights": ([P, P], c_int32),
+        "nsfrb_imager_info": ([P, POINTER(c_int32), POINTER(c_int32), POINTER(c_int64)], c_int32),
+        "nsfrb_image": ([P, P, c_int32, P, P], c_int32),
+        "nsfrb_imager_destroy": ([P], None),
         "nsfrb_clf_create": ([POINTER(nsfrb_clf_config), POINTER(c_void_p)], c_int32),
         "nsfrb_clf_n_params": ([P, POINTER(c_int64)], c_int32),
         "nsfrb_clf_set_params": ([P, P], c_int32),
@@ -246,6 +259,7 @@ class Plan:
 
     def stream_open(self, n_blk: int, hbm_reserve: int = 0) -> None:
         _check(lib.nsfrb_stream_open(self._h, int(n_blk), int(hbm_reserve)), "nsfrb_stream_open")
+        self._n_blk = int(n_blk)
 
     def stream_push(self, block: torch.Tensor, present_mask: int | None = None) -> None:
         """Push one block [n_blk, n_sub, ny, nx] FP32 (host memory)."""
@@ -269,6 +283,19 @@ class Plan:
         n = c_int64()
         _check(lib.nsfrb_stream_blocks(self._h, ctypes.byref(n)), "nsfrb_stream_blocks")
         return int(n.value)
+
+    def stream_block(self) -> torch.Tensor:
+        """The stream's device block buffer [n_blk, n_sub, ny, nx] FP32 (a view; owned by the plan)."""
+        ptr = c_void_p()
+        _check(lib.nsfrb_stream_block(self._h, ctypes.byref(ptr)), "nsfrb_stream_block")
+        c = self.cfg
+        return _device_view(ptr.value, (self._n_blk, c.n_sub, c.ny, c.nx))
+
+    def stream_push_device(self, present_mask: int | None = None, stream=None) -> None:
+        """Queue the block already written into ``stream_block()`` by work on ``stream``."""
+        m = (1 << self.cfg.n_sub) - 1 if present_mask is None else int(present_mask)
+        _check(lib.nsfrb_stream_push_device(self._h, c_uint32(m), _stream_handle(stream)),
+               "nsfrb_stream_push_device")
 
     # ------------------------------------------------------------------ lifetime
     def close(self) -> None:
@@ -383,6 +410,79 @@ def cutouts(plan: "Plan", cube: torch.Tensor, cands: torch.Tensor, d: int = 32, 
     _check(lib.nsfrb_clf_cutouts(plan.handle, _ptr(cube), _ptr(sigma), _ptr(cands), n, d, h, w, _ptr(out),
                                  _stream_handle(stream)), "nsfrb_clf_cutouts")
     return out
+
+
+class _CudaArray:
+    """Minimal __cuda_array_interface__ holder: lets torch view library-owned device memory."""
+
+    def __init__(self, ptr: int, shape):
+        self.__cuda_array_interface__ = {"data": (int(ptr), False), "shape": tuple(shape), "typestr": "<f4",
+                                         "version": 3, "strides": None}
+
+
+def _device_view(ptr: int, shape) -> torch.Tensor:
+    return torch.as_tensor(_CudaArray(ptr, shape), device="cuda")
+
+
+class Imager:
+    """``nsfrb_imager_*``: Briggs-weighted gridding + shifted inverse FFT (Sec. 2.1) on the GPU."""
+
+    def __init__(self, uv_m: np.ndarray, chan_mhz: np.ndarray, n_grid: int = 175, pixel_arcsec: float = 10.3,
+                 robust: float = -2.0, b_min_m: float = 20.0, b_max_m: float = 485.0):
+        self._uv = np.ascontiguousarray(uv_m, dtype=np.float64)
+        self._ch = np.ascontiguousarray(chan_mhz, dtype=np.float64)
+        self.n_sub, self.n_chan = self._ch.shape
+        self.n_base = self._uv.shape[0]
+        self.n_grid = int(n_grid)
+        c = nsfrb_imager_config(self.n_grid, float(pixel_arcsec), float(robust), float(b_min_m), float(b_max_m),
+                                self.n_base, self._uv.ctypes.data_as(POINTER(c_double)), self.n_sub, self.n_chan,
+                                self._ch.ctypes.data_as(POINTER(c_double)))
+        h = c_void_p()
+        _check(lib.nsfrb_imager_create(ctypes.byref(c), ctypes.byref(h)), "nsfrb_imager_create")
+        self._h = h
+
+    def weights(self) -> np.ndarray:
+        out = np.empty((self.n_sub, self.n_chan, self.n_base), np.float32)
+        _check(lib.nsfrb_imager_weights(self._h, out.ctypes.data_as(c_void_p)), "nsfrb_imager_weights")
+        return out
+
+    def info(self):
+        u, v, n = c_int32(), c_int32(), c_int64()
+        _check(lib.nsfrb_imager_info(self._h, ctypes.byref(u), ctypes.byref(v), ctypes.byref(n)), "nsfrb_imager_info")
+        return int(u.value), int(v.value), int(n.value)
+
+    def image(self, vis: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """vis: complex64 [n_t, n_sub, n_chan, n_base, 2] (or its float32 view [..., 2, 2]) on the GPU."""
+        if vis.is_complex():
+            vis = torch.view_as_real(vis)
+        shape = (self.n_sub, self.n_chan, self.n_base, 2, 2)
+        if vis.dtype != torch.float32 or not vis.is_cuda or not vis.is_contiguous() or tuple(vis.shape[1:]) != shape:
+            raise ValueError(f"visibilities must be contiguous CUDA float32 [n_t, {shape}]")
+        n_t = vis.shape[0]
+        N = self.n_grid
+        if out is None:
+            out = torch.empty((n_t, self.n_sub, N, N), dtype=torch.float32, device=vis.device)
+        if out.dtype != torch.float32 or not out.is_cuda or not out.is_contiguous() or out.numel() != n_t * self.n_sub * N * N:
+            raise ValueError("out must be contiguous CUDA float32 [n_t, n_sub, N, N]")
+        _check(lib.nsfrb_image(self._h, _ptr(vis), n_t, _ptr(out), _stream_handle(stream)), "nsfrb_image")
+        return out
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib.nsfrb_imager_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def candidates_to_device(cand: np.ndarray, device="cuda") -> torch.Tensor:

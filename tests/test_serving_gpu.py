@@ -44,11 +44,13 @@ def _window_oracle(cfg, window, n_blk, tab):
     return best
 
 
-@pytest.mark.parametrize("dtype", ["f32", "bf16"])
-def test_stream_equals_masked_window_search(native, dtype):
+@pytest.mark.parametrize("dtype,n_blk", [("f32", 12), ("bf16", 12), ("f32", 25), ("bf16", 25)])
+def test_stream_equals_masked_window_search(native, dtype, n_blk):
+    """n_blk = 25 (the paper's block) moves the window start by 100 bytes per FP32 block: the
+    search must not take the 16-byte-aligned bulk-copy path there."""
     cfg = synth.SearchConfig(ny=5, nx=7, n_t=96, dm=np.linspace(0, 1500, 20),
                              widths=np.array([1, 2, 4, 8, 16, 32, 50], np.int32), threshold=5.0)
-    n_blk, n_blocks = 12, 14
+    n_blocks = 14
     x = _series(cfg, n_blk * n_blocks, 3)
     if dtype == "bf16":
         x = x.to(torch.bfloat16).to(torch.float32)
