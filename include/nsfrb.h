@@ -317,8 +317,16 @@ nsfrb_status nsfrb_imager_info(nsfrb_imager_t im, int32_t *u_max, int32_t *v_max
  * aligned.  d_img: device FP32 [n_t][n_sub][N][N] (the serving block layout
  * when N x N is the search plan's ny x nx).  Asynchronous on `stream`.
  * Accumulates in FP32 (gridding in a fixed order: results are reproducible
- * bit for bit). */
+ * bit for bit).  The first call with more images than any before allocates
+ * the imager's workspace (n_t * n_sub * n_chan partial grids) and
+ * synchronises the device. */
 nsfrb_status nsfrb_image(nsfrb_imager_t im, const float *d_vis, int32_t n_t, float *d_img, void *stream);
+
+/* Synchronous check of the imaging calls so far: ETIMEOUT if a bulk copy of
+ * visibilities into shared memory did not complete within the kernel's 2 s
+ * wait limit (the images of that call are then incomplete; the flag is
+ * cleared), OK otherwise. */
+nsfrb_status nsfrb_imager_status(nsfrb_imager_t im);
 void nsfrb_imager_destroy(nsfrb_imager_t im);
 
 /* ---- candidate classifier (Sec. 2.3: convolutional blocks with batch

@@ -91,6 +91,7 @@ def _load() -> ctypes.CDLL:
         "nsfrb_imager_weights": ([P, P], c_int32),
         "nsfrb_imager_info": ([P, POINTER(c_int32), POINTER(c_int32), POINTER(c_int64)], c_int32),
         "nsfrb_image": ([P, P, c_int32, P, P], c_int32),
+        "nsfrb_imager_status": ([P], c_int32),
         "nsfrb_imager_destroy": ([P], None),
         "nsfrb_clf_create": ([POINTER(nsfrb_clf_config), POINTER(c_void_p)], c_int32),
         "nsfrb_clf_n_params": ([P, POINTER(c_int64)], c_int32),
@@ -466,6 +467,10 @@ class Imager:
             raise ValueError("out must be contiguous CUDA float32 [n_t, n_sub, N, N]")
         _check(lib.nsfrb_image(self._h, _ptr(vis), n_t, _ptr(out), _stream_handle(stream)), "nsfrb_image")
         return out
+
+    def status(self) -> None:
+        """Synchronous: raises NsfrbError(ETIMEOUT) if a kernel's bulk copy timed out."""
+        _check(lib.nsfrb_imager_status(self._h), "nsfrb_imager_status")
 
     def close(self) -> None:
         if getattr(self, "_h", None):

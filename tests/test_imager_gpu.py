@@ -2,8 +2,9 @@
 
 Tolerance.  Each pixel is inv_n2 (A_0 + 2 sum_u Re(A_u t_u)), A_u = sum_v G t,
 G = sum of weighted visibilities; every quantity is a sum of at most
-n = m + 2V + 2U + 8 FP32 roundings (m the most entries in one half-plane cell,
-plus the weight, twiddle and 1/N^2 roundings), so
+n = m + n_chan + 2V + 2U + 8 FP32 roundings (m the most entries in one half-plane
+cell over all channels, n_chan for adding the channels' partial grids, plus the
+weight, twiddle and 1/N^2 roundings), so
 |gpu - oracle| <= gamma_n * 2 * sum_i w_i |V_i| / N^2 with gamma_n = n u / (1 - n u),
 u = 2^-24 (summed over the subband's channels).  That worst case is loose, so the
 rms error is also held to 1e-5 of the image rms: one dropped visibility moves
@@ -54,6 +55,7 @@ def _compare(native, uv, chan, n, pix, vis_c, t_s=None, b_min=20.0, b_max=485.0,
     (t, s) pairs t_s (all if None)."""
     im = native.Imager(uv, chan, n_grid=n, pixel_arcsec=pix, robust=robust, b_min_m=b_min, b_max_m=b_max)
     gpu = im.image(vis_c.cuda()).cpu().numpy()
+    im.status()
     U, V, _ = im.info()
     wt = oi.weights(uv, chan, n, pix, robust, b_min, b_max)
     # weights: same FP64 expressions on both sides, rounded to FP32 by the library
@@ -65,7 +67,7 @@ def _compare(native, uv, chan, n, pix, vis_c, t_s=None, b_min=20.0, b_max=485.0,
     for t, s in pairs:
         ref = oi.image(vis[t:t + 1, s:s + 1], uv, chan[s:s + 1], n, pix, robust, b_min, b_max)[0, 0]
         m = _max_cell_entries(uv, chan[s], n, pix, b_min, b_max)
-        nr = m + 2 * V + 2 * U + 8
+        nr = m + chan.shape[1] + 2 * V + 2 * U + 8
         gam = nr * U32 / (1 - nr * U32)
         vsum = np.abs(vis[t, s, :, :, 0].astype(np.complex128) + vis[t, s, :, :, 1])
         tol = gam * 2.0 * float((wt[s] * vsum).sum()) / n**2
