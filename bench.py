@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--classifier-samples", type=int, default=6000,
                     help="labelled cutouts for the classifier section (0: skip)")
     ap.add_argument("--classifier-epochs", type=int, default=2)
+    ap.add_argument("--only", default="all", choices=["all", "imager"],
+                    help="imager: run only the imager section (one JSON object) and exit")
     ap.add_argument("--imager-steps", type=int, default=20,
                     help="timed launches of the imager section, one 25-sample block each (0: skip)")
     ap.add_argument("--seed", type=int, default=0)
@@ -93,6 +95,19 @@ def make_cube(native, synth, cfg, seed, device, dtype):
 # DRAM bytes (read + write) per 301x301 FP32 launch from the ncu capture summarised in
 # profiles/search_kernel_full_window.md, valid for the kernel source with this sha256 prefix.
 NCU_TRAFFIC = {"sha256_16": "d2a2366b1a982ccb", "bytes": 7.034e9, "workload": (301, 301, "f32")}
+
+
+# DRAM bytes of one imager call (grid_kernel + transform_kernel) from the ncu launch list of the
+# committed kernels (paper block: 25 x 16 x 8 x 3321 x 2 pol, 175 px); ncu flushes the caches
+# before each kernel, so the transform re-reads the 15.6 MB of partial grids from DRAM there.
+IMG_NCU_TRAFFIC = {"sha256_16": "efc27e98ac335103", "bytes": 181822464 + 6787328 + 15642112 + 203264}
+
+
+def imager_traffic():
+    import hashlib
+    with open(os.path.join(ROOT, "paper_2510_18136_gb300", "csrc", "imager.cu"), "rb") as fh:
+        digest = hashlib.sha256(fh.read()).hexdigest()[:16]
+    return IMG_NCU_TRAFFIC["bytes"] if digest == IMG_NCU_TRAFFIC["sha256_16"] else None
 
 
 def measured_traffic(ny, nx, dtype):
@@ -393,8 +408,9 @@ def imager_section(native, steps: int, seed: int = 0):
             "ms_per_block": t * 1e3, "images_per_s": n_t * n_sub / t,
             "visibilities_per_s": n_t * n_sub * n_chan * len(uv) * 2 / t,
             "roofline": {"bound": "hbm", "achieved": alg / t / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                         "frac": alg / t / 1e9 / pk["hbm_gbs"], "bytes_per_launch": alg, "kernel": "image_kernel",
-                         "traffic": None},
+                         "frac": alg / t / 1e9 / pk["hbm_gbs"], "bytes_per_launch": alg,
+                         "kernel": "grid_kernel + transform_kernel (one nsfrb_image call)",
+                         "traffic": imager_traffic()},
             "l2": "256 MB buffer written between launches",
             "cpu_baseline": {"value": 1.0 / t_cpu, "unit": "images/s", "cores": 1, "kind": "oracle",
                              "sample": f"{len(pairs)} images of the block, FP64 numpy"}}
@@ -409,6 +425,10 @@ def main():
     import torch
     import torch.distributed as dist
     from paper_2510_18136_gb300 import native, synth
+
+    if args.only == "imager":
+        print(json.dumps({"imager": imager_section(native, args.imager_steps, seed=args.seed)}), flush=True)
+        return 0
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
