@@ -83,6 +83,7 @@ struct SearchParams {
     int32_t gen_wi[kMaxW];
     int32_t n_dm;
     int32_t new_blk;       // > 0: only trials that end in the last new_blk samples
+    int32_t pipe;          // 1: barrier-free kernel (stage 1, KNOWN noise, candidates only)
     // ---- outputs (indexed by absolute pixel)
     PixRec *rec;
     float *full_snr;       // [pix][n_dm][n_w] or nullptr
@@ -113,9 +114,10 @@ __host__ __device__ inline SmemLayout smem_layout(const SearchParams &p, int C) 
     // MAD histograms: in the staging buffer of the current item when staging, else own space
     if (p.noise_mode == 1 && p.stage != 2) o += sizeof(uint32_t) * (size_t)kWarps * kHistBins;
     L.wbest = o;
-    o += sizeof(PixRec) * kWarps;
+    const size_t n_slots = p.pipe ? 2 : 1;   // the barrier-free kernel keeps two pixels' records
+    o += sizeof(PixRec) * kWarps * n_slots;
     L.sinv = o;
-    o += sizeof(float) * kMaxW + sizeof(int32_t) * 4;
+    o += sizeof(float) * kMaxW * n_slots + sizeof(int32_t) * 4;
     o = align_up(o, 8);
     L.bar = o;
     o += sizeof(unsigned long long) * 2;

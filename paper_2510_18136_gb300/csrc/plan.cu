@@ -121,6 +121,9 @@ bool choose_stage(const nsfrb_plan_s *pl, SearchParams &sp, size_t &smem) {
     for (int st = want; st >= 0; st = (st == 2 ? 0 : st - 1)) {
         sp.stage = st;
         sp.stg_pitch = (st == 2) ? static_cast<int32_t>(align_up(static_cast<size_t>(7 + n_t) * 2, 16)) : 0;
+        // the barrier-free kernel: FP32 rows copied straight in, KNOWN noise, records only
+        sp.pipe = (st == 1 && sp.noise_mode == 0 && !sp.full_snr && sp.new_blk == 0) ? 1 : 0;
+        if (sp.pipe && smem_layout(sp, pl->C).total > static_cast<size_t>(pl->max_smem)) sp.pipe = 0;
         const SmemLayout L = smem_layout(sp, pl->C);
         if (L.total <= static_cast<size_t>(pl->max_smem)) {
             smem = L.total;

@@ -284,6 +284,201 @@ __device__ __forceinline__ int warp_min(int v) {
     return v;
 }
 
+// ------------------------------------------------------------------ one warp, one pixel
+
+// The search of one warp over the distinct DM rows [u_lo, u_hi) of one pixel whose
+// subband rows are in xs (pitch Tp, -inf beyond the window): de-dispersion by row
+// differences, prefix sums, the boxcars of every width class, the warp arg-max and,
+// when a row improves the warp's best, the earliest sample reaching it (re-evaluated
+// with the same operations).  FULL also writes every (DM, width) result of the rows.
+// Returns the warp's best (snr, distinct row u, width index, t) on every lane.
+template <int C, bool FULL>
+__device__ __forceinline__ PixRec search_rows(const SearchParams &p, const float *xs, float *Pw, const float *s_inv,
+                                              const int32_t *s_info, const int32_t *s_delta,
+                                              const int32_t *s_shift, int u_lo, int u_hi, int64_t pix,
+                                              int lane) {
+    constexpr int SH = (C < kSmallMax) ? C : kSmallMax;
+    const int n_sub = p.n_sub, n_t = p.n_t, Tp = p.Tp;
+    const int t0 = lane * C;
+    float bsnr = neg_inf();
+    int bu = -1, bwi = -1, bt = -1;
+    float D[C];
+#pragma unroll 1
+    for (int u = u_lo; u < u_hi; ++u) {
+        const int32_t *info = s_info + u * kInfo;
+        if (u == u_lo) {
+#pragma unroll
+            for (int c = 0; c < C; ++c) D[c] = 0.0f;
+            const int32_t *sh = s_shift + u * n_sub;
+#pragma unroll 1
+            for (int k = 0; k < n_sub; ++k) {
+                const float *xr = xs + (size_t)k * Tp + t0 + sh[k];
+#pragma unroll
+                for (int c = 0; c < C; ++c) D[c] += xr[c];
+            }
+        } else {
+            const int d0 = info[UI_DOFF], nd = info[UI_ND];
+#pragma unroll 1
+            for (int e = d0; e < d0 + nd; ++e) {
+                const uint32_t pk = static_cast<uint32_t>(s_delta[e]);
+                const int k = pk & 63u, so = (pk >> 6) & 0x1fffu, sn = pk >> 19;
+                const float *xo = xs + (size_t)k * Tp + t0 + so;
+                const float *xn = xs + (size_t)k * Tp + t0 + sn;
+#pragma unroll
+                for (int c = 0; c < C; ++c) D[c] = (D[c] + xn[c]) - xo[c];
+            }
+        }
+        const int L = n_t - info[UI_SMAX];
+
+        // in-lane prefix, warp scan of lane totals, P to shared memory
+        const bool masked = p.new_blk > 0;
+        float ls = neg_inf();
+        int lw = -1;
+        auto consider = [&](int wi, float m) {
+            const float s = m * s_inv[wi];
+            if (s > ls || (s == ls && wi < lw)) {
+                ls = s;
+                lw = wi;
+            }
+        };
+        // FULL mode: the S/N of (row u, width wi) reduced over the warp, and its TOA
+        auto write_full = [&](int wi, float s, int t) {
+            if (lane == 0) {
+                const int fd = info[UI_FIRST_D], ndm = info[UI_N_D];
+                for (int d = fd; d < fd + ndm; ++d) {
+                    const int64_t o = (pix * p.n_dm + d) * p.n_w + wi;
+                    p.full_snr[o] = s;
+                    p.full_t[o] = static_cast<int16_t>(t == INT_MAX ? -1 : t);
+                }
+            }
+        };
+        {
+            float Lp[C + 1];
+            const float tot = lane_prefix<C>(D, Lp);
+            float inc = tot;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const float y = __shfl_up_sync(kFull, inc, o);
+                if (lane >= o) inc += y;
+            }
+            float carry = __shfl_up_sync(kFull, inc, 1);
+            if (lane == 0) carry = 0.0f;
+#pragma unroll
+            for (int c = 0; c < C; ++c) Pw[t0 + c] = carry + Lp[c];
+            if (!masked && p.has_small) {
+                // power-of-two widths <= min(C, 16): in-lane, compile-time unrolled and
+                // branch-free (absent widths are computed and masked); ascending width
+                // order with a strict '>' keeps the smallest width index on ties
+                float H[SH + 1];
+                lane_halo<C, SH>(Lp, tot, lane, H);
+#define NSFRB_SMALL_J(J)                                                                                   \
+    if constexpr (pow2_class(C, J) == WC_SMALL) {                                                         \
+const int wi = p.pow2_wi[J];                                                                       \
+const float m = small_max_w<C, SH, (1 << J)>(Lp, H);                                              \
+const float s = (wi >= 0) ? m * s_inv[wi < 0 ? 0 : wi] : neg_inf();                              \
+if (s > ls) {                                                                                      \
+    ls = s;                                                                                        \
+    lw = wi;                                                                                       \
+}                                                                                                  \
+if constexpr (FULL) {                                                                              \
+    if (wi >= 0) {                                                                                 \
+        const float mw = warp_max(m), sw = mw * s_inv[wi];                                        \
+        int t = INT_MAX;                                                                           \
+        if (mw != neg_inf()) t = warp_min(small_find_w<C, SH, (1 << J)>(Lp, H, s_inv[wi], sw, t0)); \
+        write_full(wi, sw, t);                                                                     \
+    }                                                                                              \
+}                                                                                                  \
+    }
+                NSFRB_POW2(NSFRB_SMALL_J)
+#undef NSFRB_SMALL_J
+            }
+        }
+        __syncwarp();
+        if (!masked && p.has_large) {
+            // power-of-two widths 32 * M with M < C: lane-strided, compile-time unrolled
+            float Ps[C];
+#pragma unroll
+            for (int i = 0; i < C; ++i) Ps[i] = Pw[32 * i + lane];
+#define NSFRB_LARGE_J(J)                                                                                   \
+    if constexpr (pow2_class(C, J) == WC_LARGE) {                                                         \
+const int wi = p.pow2_wi[J];                                                                       \
+const float m = large_max_m<C, ((1 << J) >> 5)>(Ps);                                              \
+const float s = (wi >= 0) ? m * s_inv[wi < 0 ? 0 : wi] : neg_inf();                              \
+if (s > ls) {                                                                                      \
+    ls = s;                                                                                        \
+    lw = wi;                                                                                       \
+}                                                                                                  \
+if constexpr (FULL) {                                                                              \
+    if (wi >= 0) {                                                                                 \
+        const float mw = warp_max(m), sw = mw * s_inv[wi];                                        \
+        int t = INT_MAX;                                                                           \
+        if (mw != neg_inf()) t = warp_min(large_find_m<C, ((1 << J) >> 5)>(Ps, s_inv[wi], sw, lane)); \
+        write_full(wi, sw, t);                                                                     \
+    }                                                                                              \
+}                                                                                                  \
+    }
+            NSFRB_POW2(NSFRB_LARGE_J)
+#undef NSFRB_LARGE_J
+        }
+        // every other width (and every width of a masked search) from shared memory
+        const int n_gen = masked ? p.n_w : p.n_gen;
+#pragma unroll 1
+        for (int g = 0; g < n_gen; ++g) {
+            const int wi = masked ? g : p.gen_wi[g];
+            const int w = p.widths[wi];
+            const int tl = masked ? max(0, L - w - p.new_blk + 1) : 0;
+            const float m = generic_max(Pw, w, L, tl, lane);
+            consider(wi, m);
+            if constexpr (FULL) {
+                const float mw = warp_max(m), sw = mw * s_inv[wi];
+                int t = INT_MAX;
+                if (mw != neg_inf()) t = warp_min(generic_find(Pw, w, L, tl, lane, s_inv[wi], sw));
+                write_full(wi, sw, t);
+            }
+        }
+
+        // warp arg-max over (S/N, width index)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float os = __shfl_xor_sync(kFull, ls, o);
+            const int ow = __shfl_xor_sync(kFull, lw, o);
+            if (os > ls || (os == ls && ow < lw && ow >= 0)) {
+                ls = os;
+                lw = ow;
+            }
+        }
+        if (ls > bsnr) {
+            // earliest sample reaching this S/N, re-evaluated exactly as above
+            // (the prefix and halo are rebuilt from D: same operations, same values)
+            const int w = p.widths[lw];
+            const float inv = s_inv[lw];
+            int t;
+            if (masked || p.wclass[lw] == WC_GENERIC) {
+                const int tl = masked ? max(0, L - w - p.new_blk + 1) : 0;
+                t = generic_find(Pw, w, L, tl, lane, inv, ls);
+            } else if (p.wclass[lw] == WC_SMALL) {
+                float Lp[C + 1];
+                float H[SH + 1];
+                const float tot = lane_prefix<C>(D, Lp);
+                lane_halo<C, SH>(Lp, tot, lane, H);
+                t = small_find<C, SH>(w, Lp, H, inv, ls, t0);
+            } else {
+                float Ps[C];
+#pragma unroll
+                for (int i = 0; i < C; ++i) Ps[i] = Pw[32 * i + lane];
+                t = large_find<C>(w >> 5, Ps, inv, ls, lane);
+            }
+            t = warp_min(t);
+            bsnr = ls;
+            bu = u;
+            bwi = lw;
+            bt = t;
+        }
+        __syncwarp();
+    }
+    return PixRec{bsnr, bu, bwi, bt};
+}
+
 // ------------------------------------------------------------------ the kernel
 
 template <int C, bool FULL>
@@ -462,184 +657,11 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel(const __grid_consta
         }
 
         // ---- per-warp search over its rows
-        float bsnr = neg_inf();
-        int bu = -1, bwi = -1, bt = -1;
-        float D[C];
-        if (!bad_pixel) {
-#pragma unroll 1
-            for (int u = u_lo; u < u_hi; ++u) {
-                const int32_t *info = s_info + u * kInfo;
-                if (u == u_lo) {
-#pragma unroll
-                    for (int c = 0; c < C; ++c) D[c] = 0.0f;
-                    const int32_t *sh = s_shift + u * n_sub;
-#pragma unroll 1
-                    for (int k = 0; k < n_sub; ++k) {
-                        const float *xr = xs + (size_t)k * Tp + t0 + sh[k];
-#pragma unroll
-                        for (int c = 0; c < C; ++c) D[c] += xr[c];
-                    }
-                } else {
-                    const int d0 = info[UI_DOFF], nd = info[UI_ND];
-#pragma unroll 1
-                    for (int e = d0; e < d0 + nd; ++e) {
-                        const uint32_t pk = static_cast<uint32_t>(s_delta[e]);
-                        const int k = pk & 63u, so = (pk >> 6) & 0x1fffu, sn = pk >> 19;
-                        const float *xo = xs + (size_t)k * Tp + t0 + so;
-                        const float *xn = xs + (size_t)k * Tp + t0 + sn;
-#pragma unroll
-                        for (int c = 0; c < C; ++c) D[c] = (D[c] + xn[c]) - xo[c];
-                    }
-                }
-                const int L = n_t - info[UI_SMAX];
-
-                // in-lane prefix, warp scan of lane totals, P to shared memory
-                const bool masked = p.new_blk > 0;
-                float ls = neg_inf();
-                int lw = -1;
-                auto consider = [&](int wi, float m) {
-                    const float s = m * s_inv[wi];
-                    if (s > ls || (s == ls && wi < lw)) {
-                        ls = s;
-                        lw = wi;
-                    }
-                };
-                // FULL mode: the S/N of (row u, width wi) reduced over the warp, and its TOA
-                auto write_full = [&](int wi, float s, int t) {
-                    if (lane == 0) {
-                        const int fd = info[UI_FIRST_D], ndm = info[UI_N_D];
-                        for (int d = fd; d < fd + ndm; ++d) {
-                            const int64_t o = (pix * p.n_dm + d) * p.n_w + wi;
-                            p.full_snr[o] = s;
-                            p.full_t[o] = static_cast<int16_t>(t == INT_MAX ? -1 : t);
-                        }
-                    }
-                };
-                {
-                    float Lp[C + 1];
-                    const float tot = lane_prefix<C>(D, Lp);
-                    float inc = tot;
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const float y = __shfl_up_sync(kFull, inc, o);
-                        if (lane >= o) inc += y;
-                    }
-                    float carry = __shfl_up_sync(kFull, inc, 1);
-                    if (lane == 0) carry = 0.0f;
-#pragma unroll
-                    for (int c = 0; c < C; ++c) Pw[t0 + c] = carry + Lp[c];
-                    if (!masked && p.has_small) {
-                        // power-of-two widths <= min(C, 16): in-lane, compile-time unrolled and
-                        // branch-free (absent widths are computed and masked); ascending width
-                        // order with a strict '>' keeps the smallest width index on ties
-                        float H[SH + 1];
-                        lane_halo<C, SH>(Lp, tot, lane, H);
-#define NSFRB_SMALL_J(J)                                                                                   \
-    if constexpr (pow2_class(C, J) == WC_SMALL) {                                                         \
-        const int wi = p.pow2_wi[J];                                                                       \
-        const float m = small_max_w<C, SH, (1 << J)>(Lp, H);                                              \
-        const float s = (wi >= 0) ? m * s_inv[wi < 0 ? 0 : wi] : neg_inf();                              \
-        if (s > ls) {                                                                                      \
-            ls = s;                                                                                        \
-            lw = wi;                                                                                       \
-        }                                                                                                  \
-        if constexpr (FULL) {                                                                              \
-            if (wi >= 0) {                                                                                 \
-                const float mw = warp_max(m), sw = mw * s_inv[wi];                                        \
-                int t = INT_MAX;                                                                           \
-                if (mw != neg_inf()) t = warp_min(small_find_w<C, SH, (1 << J)>(Lp, H, s_inv[wi], sw, t0)); \
-                write_full(wi, sw, t);                                                                     \
-            }                                                                                              \
-        }                                                                                                  \
-    }
-                        NSFRB_POW2(NSFRB_SMALL_J)
-#undef NSFRB_SMALL_J
-                    }
-                }
-                __syncwarp();
-                if (!masked && p.has_large) {
-                    // power-of-two widths 32 * M with M < C: lane-strided, compile-time unrolled
-                    float Ps[C];
-#pragma unroll
-                    for (int i = 0; i < C; ++i) Ps[i] = Pw[32 * i + lane];
-#define NSFRB_LARGE_J(J)                                                                                   \
-    if constexpr (pow2_class(C, J) == WC_LARGE) {                                                         \
-        const int wi = p.pow2_wi[J];                                                                       \
-        const float m = large_max_m<C, ((1 << J) >> 5)>(Ps);                                              \
-        const float s = (wi >= 0) ? m * s_inv[wi < 0 ? 0 : wi] : neg_inf();                              \
-        if (s > ls) {                                                                                      \
-            ls = s;                                                                                        \
-            lw = wi;                                                                                       \
-        }                                                                                                  \
-        if constexpr (FULL) {                                                                              \
-            if (wi >= 0) {                                                                                 \
-                const float mw = warp_max(m), sw = mw * s_inv[wi];                                        \
-                int t = INT_MAX;                                                                           \
-                if (mw != neg_inf()) t = warp_min(large_find_m<C, ((1 << J) >> 5)>(Ps, s_inv[wi], sw, lane)); \
-                write_full(wi, sw, t);                                                                     \
-            }                                                                                              \
-        }                                                                                                  \
-    }
-                    NSFRB_POW2(NSFRB_LARGE_J)
-#undef NSFRB_LARGE_J
-                }
-                // every other width (and every width of a masked search) from shared memory
-                const int n_gen = masked ? p.n_w : p.n_gen;
-#pragma unroll 1
-                for (int g = 0; g < n_gen; ++g) {
-                    const int wi = masked ? g : p.gen_wi[g];
-                    const int w = p.widths[wi];
-                    const int tl = masked ? max(0, L - w - p.new_blk + 1) : 0;
-                    const float m = generic_max(Pw, w, L, tl, lane);
-                    consider(wi, m);
-                    if constexpr (FULL) {
-                        const float mw = warp_max(m), sw = mw * s_inv[wi];
-                        int t = INT_MAX;
-                        if (mw != neg_inf()) t = warp_min(generic_find(Pw, w, L, tl, lane, s_inv[wi], sw));
-                        write_full(wi, sw, t);
-                    }
-                }
-
-                // warp arg-max over (S/N, width index)
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    const float os = __shfl_xor_sync(kFull, ls, o);
-                    const int ow = __shfl_xor_sync(kFull, lw, o);
-                    if (os > ls || (os == ls && ow < lw && ow >= 0)) {
-                        ls = os;
-                        lw = ow;
-                    }
-                }
-                if (ls > bsnr) {
-                    // earliest sample reaching this S/N, re-evaluated exactly as above
-                    // (the prefix and halo are rebuilt from D: same operations, same values)
-                    const int w = p.widths[lw];
-                    const float inv = s_inv[lw];
-                    int t;
-                    if (masked || p.wclass[lw] == WC_GENERIC) {
-                        const int tl = masked ? max(0, L - w - p.new_blk + 1) : 0;
-                        t = generic_find(Pw, w, L, tl, lane, inv, ls);
-                    } else if (p.wclass[lw] == WC_SMALL) {
-                        float Lp[C + 1];
-                        float H[SH + 1];
-                        const float tot = lane_prefix<C>(D, Lp);
-                        lane_halo<C, SH>(Lp, tot, lane, H);
-                        t = small_find<C, SH>(w, Lp, H, inv, ls, t0);
-                    } else {
-                        float Ps[C];
-#pragma unroll
-                        for (int i = 0; i < C; ++i) Ps[i] = Pw[32 * i + lane];
-                        t = large_find<C>(w >> 5, Ps, inv, ls, lane);
-                    }
-                    t = warp_min(t);
-                    bsnr = ls;
-                    bu = u;
-                    bwi = lw;
-                    bt = t;
-                }
-                __syncwarp();
-            }
-        }
+        PixRec wr{neg_inf(), -1, -1, -1};
+        if (!bad_pixel)
+            wr = search_rows<C, FULL>(p, xs, Pw, s_inv, s_info, s_delta, s_shift, u_lo, u_hi, pix, lane);
+        const float bsnr = wr.snr;
+        const int bu = wr.dm_idx, bwi = wr.w_idx, bt = wr.t_idx;
         // FULL mode: DM rows that have no trial at all
         if (p.full_snr && warp == 0) {
             for (int u = bad_pixel ? 0 : n_ua; u < p.n_u; ++u) {
@@ -672,11 +694,144 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel(const __grid_consta
     }
 }
 
+
+// ------------------------------------------------------------------ barrier-free kernel
+
+// Same search (FP32 rows bulk-copied straight into a double buffer, KNOWN noise, per-pixel
+// records only) without CTA barriers between pixels.  Every warp walks the CTA's pixels on
+// its own; on the CTA's i-th pixel warp w takes row group (w + i) mod kWarps, so the groups
+// with one row more rotate over the warps.  A warp publishes its group's best and counts
+// itself done; the last warp of a pixel combines the groups in row order (the DM tie rule),
+// writes the pixel's record, and starts the copy of the pixel two ahead into the buffer it
+// frees (with that pixel's 1 / (sigma sqrt(w))).  Warps drift apart by at most one pixel.
+template <int C>
+__global__ void __launch_bounds__(kThreads, 1) search_kernel_pipe(const __grid_constant__ SearchParams p) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const SmemLayout lay = smem_layout(p, C);
+    int32_t *s_table = reinterpret_cast<int32_t *>(smem + lay.table);
+    float *s_xs = reinterpret_cast<float *>(smem + lay.xs);
+    float *s_pbuf = reinterpret_cast<float *>(smem + lay.pbuf);
+    PixRec *s_wbest = reinterpret_cast<PixRec *>(smem + lay.wbest);        // [2][kWarps] by row group
+    float *s_inv = reinterpret_cast<float *>(smem + lay.sinv);             // [2][kMaxW]
+    int32_t *s_word = reinterpret_cast<int32_t *>(smem + lay.sinv + sizeof(float) * kMaxW * 2);
+    int32_t *s_cnt = s_word;          // [2] warps done with the pixel in each buffer
+    int32_t *s_flag = s_word + 2;     // error seen by a warp
+    unsigned long long *s_bar = reinterpret_cast<unsigned long long *>(smem + lay.bar);
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int n_sub = p.n_sub, n_t = p.n_t, Tp = p.Tp;
+    const int t_off = p.t_off_dev ? *p.t_off_dev : p.t_off;
+
+    const int table_words = p.n_u * kInfo + p.n_deltas + p.n_u * n_sub;
+    for (int i = tid; i < table_words; i += kThreads) s_table[i] = p.table[i];
+    const int32_t *s_info = s_table;
+    const int32_t *s_delta = s_table + p.n_u * kInfo;
+    const int32_t *s_shift = s_delta + p.n_deltas;
+    for (int b = 0; b < 2; ++b)
+        for (int i = tid; i < n_sub * (Tp - n_t); i += kThreads) {
+            const int k = i / (Tp - n_t), t = n_t + i % (Tp - n_t);
+            s_xs[(size_t)b * n_sub * Tp + (size_t)k * Tp + t] = neg_inf();
+        }
+
+    int64_t n_items = p.n_items;
+    if (p.n_items_dev) n_items = *p.n_items_dev;
+    auto item_pixel = [&](int64_t it) -> int64_t {
+        return p.pix_list ? static_cast<int64_t>(p.pix_list[it]) : p.pix0 + it;
+    };
+    // one warp: 1 / (sigma sqrt(w)) of item `it` into slot b, then its rows into buffer b
+    // (lane 0 arms the barrier, lane k copies subband k)
+    auto issue_warp = [&](int64_t it, int b) {
+        const int64_t pix = item_pixel(it);
+        if (lane < p.n_w) {
+            const float sg = p.sigma ? p.sigma[pix] : p.sigma_default;
+            s_inv[b * kMaxW + lane] = 1.0f / (sg * sqrtf(static_cast<float>(p.widths[lane])));
+        }
+        __syncwarp();
+        if (lane == 0) mbar_expect_tx(&s_bar[b], static_cast<uint32_t>(n_sub * n_t * 4));
+        __syncwarp();
+        const float *src = static_cast<const float *>(p.cube);
+        const int64_t row0 = (pix - p.cube_pix0) * n_sub;
+        float *dst = s_xs + (size_t)b * n_sub * Tp;
+        for (int k = lane; k < n_sub; k += 32)
+            bulk_g2s(dst + (size_t)k * Tp, src + (row0 + k) * p.row_len + t_off, static_cast<uint32_t>(n_t * 4),
+                     &s_bar[b]);
+    };
+    if (tid == 0) {
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
+        s_cnt[0] = 0;
+        s_cnt[1] = 0;
+        s_flag[0] = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_proxy_async();
+    }
+    __syncthreads();
+    if (warp == 0) {
+        if (blockIdx.x < n_items) issue_warp(blockIdx.x, 0);
+        if (blockIdx.x + gridDim.x < n_items) issue_warp(blockIdx.x + gridDim.x, 1);
+    }
+
+    const int n_ua = p.n_u_active;
+    float *Pw = s_pbuf + (size_t)warp * 32 * C;
+    int issued_last = -1;   // local index of the last item whose copy this warp started
+    int i = 0;
+    for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x, ++i) {
+        const int b = i & 1;
+        if (*reinterpret_cast<volatile int32_t *>(s_flag)) break;
+        if (!mbar_wait(&s_bar[b], static_cast<uint32_t>(i >> 1) & 1u)) {
+            if (lane == 0) {
+                atomicOr(s_flag, ERR_WAIT_TIMEOUT);
+                atomicOr(p.err, ERR_WAIT_TIMEOUT);
+            }
+            break;
+        }
+        const int g = (warp + i) % kWarps;
+        const int u_lo = (g * n_ua) / kWarps, u_hi = ((g + 1) * n_ua) / kWarps;
+        const int64_t pix = item_pixel(it);
+        const PixRec wr = search_rows<C, false>(p, s_xs + (size_t)b * n_sub * Tp, Pw, s_inv + b * kMaxW, s_info,
+                                                s_delta, s_shift, u_lo, u_hi, pix, lane);
+        // publish; this warp's reads of buffer b are done before the copy that refills it
+        fence_proxy_async();
+        int last = 0;
+        if (lane == 0) {
+            s_wbest[b * kWarps + g] = wr;
+            __threadfence_block();
+            last = atomicAdd(&s_cnt[b], 1) == kWarps - 1;
+            __threadfence_block();
+        }
+        last = __shfl_sync(kFull, last, 0);
+        if (last) {
+            if (lane == 0) {
+                PixRec best{neg_inf(), -1, -1, -1};
+                for (int q = 0; q < kWarps; ++q) {
+                    const PixRec r = s_wbest[b * kWarps + q];
+                    if (r.snr > best.snr) best = r;
+                }
+                if (best.dm_idx >= 0) best.dm_idx = s_info[best.dm_idx * kInfo + UI_FIRST_D];
+                p.rec[pix] = best;
+                s_cnt[b] = 0;
+            }
+            __syncwarp();
+            const int64_t nxt = it + 2 * (int64_t)gridDim.x;
+            if (nxt < n_items) {
+                issue_warp(nxt, b);
+                issued_last = i + 2;
+            }
+        }
+        __syncwarp();
+    }
+    // after an error: wait (bounded) for copies this warp started that may still be in flight
+    if (*reinterpret_cast<volatile int32_t *>(s_flag) && lane == 0 && issued_last >= 0)
+        mbar_wait(&s_bar[issued_last & 1], static_cast<uint32_t>(issued_last >> 1) & 1u);
+}
+
 }  // namespace dev
 
 #define NSFRB_INSTANTIATE_SEARCH(CC)                                                           \
     cudaError_t launch_search_c##CC(const SearchParams &p, int grid, size_t smem, cudaStream_t s) { \
-        if (p.full_snr)                                                                        \
+        if (p.pipe)                                                                            \
+            dev::search_kernel_pipe<CC><<<grid, kThreads, smem, s>>>(p);                       \
+        else if (p.full_snr)                                                                   \
             dev::search_kernel<CC, true><<<grid, kThreads, smem, s>>>(p);                      \
         else                                                                                   \
             dev::search_kernel<CC, false><<<grid, kThreads, smem, s>>>(p);                     \
@@ -685,6 +840,9 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel(const __grid_consta
     cudaError_t prepare_search_c##CC(size_t smem) {                                            \
         cudaError_t e = cudaFuncSetAttribute(dev::search_kernel<CC, false>,                    \
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        if (e != cudaSuccess) return e;                                                        \
+        e = cudaFuncSetAttribute(dev::search_kernel_pipe<CC>,                                  \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);      \
         if (e != cudaSuccess) return e;                                                        \
         return cudaFuncSetAttribute(dev::search_kernel<CC, true>,                              \
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);   \
