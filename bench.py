@@ -94,7 +94,7 @@ def make_cube(native, synth, cfg, seed, device, dtype):
 
 # DRAM bytes (read + write) per 301x301 FP32 launch from the ncu capture summarised in
 # profiles/search_kernel_full_window.md, valid for the kernel source with this sha256 prefix.
-NCU_TRAFFIC = {"sha256_16": "d2a2366b1a982ccb", "bytes": 7.034e9, "workload": (301, 301, "f32")}
+NCU_TRAFFIC = {"sha256_16": "a05ae0d93b5c357a", "bytes": 7.034e9, "workload": (301, 301, "f32")}
 
 
 # DRAM bytes of one imager call (grid_kernel + transform_kernel) from the ncu launch list of the
@@ -529,7 +529,8 @@ def main():
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                      "unit": "TFLOP/s", "frac": achieved / peak_ops,
                      "traffic": measured_traffic(cfg.ny, cfg.nx, args.dtype),
-                     "kernel": "search_kernel", "kernel_ms": kern_s * 1e3,
+                     "kernel": "search_kernel_pipe<39>" if args.dtype == "f32" else "search_kernel<39, false>",
+                     "kernel_ms": kern_s * 1e3,
                      "ops_per_launch": ops, "peak_basis": f"{n_sm} SM x 128 FP32 lanes x "
                      f"{pk['sm_max_mhz']:.0f} MHz ({pk['source']} max clock)"},
         "hbm": {"achieved_gbs": hbm_gbs, "peak_gbs": pk["hbm_gbs"], "frac": hbm_gbs / pk["hbm_gbs"],
