@@ -4,9 +4,10 @@
 // on the GPU by the kernels in this file.
 //
 // Layout: activations channels-last [B][D][H][W][C] (D = time), BF16 between
-// layers; convolutions are GEMMs over im2col rows with BF16 tensor-core MMA
-// and FP32 accumulation (gemm.cuh); batch-norm statistics, the head, the loss
-// and Adam run in FP32.  The flat FP32 parameter vector has the layout
+// layers; convolutions are GEMMs over the (never stored) im2col rows, gathered
+// tile by tile from the activations, with BF16 tensor-core MMA and FP32
+// accumulation (gemm.cuh); batch-norm statistics, the head, the loss and Adam
+// run in FP32.  The flat FP32 parameter vector has the layout
 //   for l = 0..3: W_l[C_l][27][C_{l-1}], gamma_l[C_l], beta_l[C_l];
 //   fc1_w[F][Fin], fc1_b[F], fc2_w[F], fc2_b[1]
 // (tap k = (kz*3 + ky)*3 + kx; Fin = D/16 * H/16 * W/16 * C_3).
@@ -46,30 +47,6 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
 }
 
 // ------------------------------------------------------------------ kernels
-
-// col[p][(k, ci)] = in[b][z+kz-1][y+ky-1][x+kx-1][ci] (zero outside); C % 8 == 0.
-__global__ void im2col3d_kernel(const bf16 *__restrict__ in, bf16 *__restrict__ col, int B, int D, int H, int W,
-                                int C) {
-    const int chunks = C / 8;
-    const int64_t total = static_cast<int64_t>(B) * D * H * W * 27 * chunks;
-    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < total;
-         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int ch = static_cast<int>(i % chunks);
-        int64_t r = i / chunks;
-        const int k = static_cast<int>(r % 27);
-        const int64_t p = r / 27;
-        const int x = static_cast<int>(p % W);
-        const int y = static_cast<int>((p / W) % H);
-        const int z = static_cast<int>((p / (static_cast<int64_t>(W) * H)) % D);
-        const int64_t b = p / (static_cast<int64_t>(W) * H * D);
-        const int kz = k / 9, ky = (k / 3) % 3, kx = k % 3;
-        const int zz = z + kz - 1, yy = y + ky - 1, xx = x + kx - 1;
-        uint4 v = make_uint4(0, 0, 0, 0);
-        if (zz >= 0 && zz < D && yy >= 0 && yy < H && xx >= 0 && xx < W)
-            v = *reinterpret_cast<const uint4 *>(in + (((b * D + zz) * H + yy) * W + xx) * C + ch * 8);
-        *reinterpret_cast<uint4 *>(col + (p * 27 + k) * C + ch * 8) = v;
-    }
-}
 
 // Per-block partial sums of y[p][c] and y^2 over rows (FP32 within a block).
 __global__ void bn_partial_kernel(const float *__restrict__ y, int64_t P, int C, int rows_per_block,
@@ -469,12 +446,12 @@ struct nsfrb_clf_s {
     uint8_t *arg[4] = {};
     float *y[4] = {};
     float *mean[4] = {}, *rstd[4] = {};
-    __nv_bfloat16 *col = nullptr, *dyb = nullptr;
+    __nv_bfloat16 *dyb = nullptr;
     float *dz = nullptr, *dact = nullptr, *part = nullptr;
     float *feat = nullptr, *h1 = nullptr, *h1d = nullptr, *logit = nullptr, *loss_terms = nullptr, *loss = nullptr;
     float *dh1 = nullptr;
     float *labels_zero = nullptr;
-    int64_t col_elems = 0, zmax = 0, dact_elems = 0;
+    int64_t zmax = 0, dact_elems = 0;
     int part_blocks = 0;
     nsfrb_status latched = NSFRB_OK;
 };
@@ -498,27 +475,42 @@ nsfrb_status clf_fail(nsfrb_status st, const std::string &msg) {
 
 constexpr int kPartRows = 2048;
 
-nsfrb_status gemm_nt(int64_t M, int N, int K, const bf16 *A, const bf16 *B, float *C, cudaStream_t s) {
-    const dim3 grid(static_cast<unsigned>((M + 127) / 128), static_cast<unsigned>((N + 63) / 64), 1);
+// C[M][N] = A[M][K] B[N][K]^T; with gx.x set, A is the im2col matrix of gx (gathered).
+template <int G>
+nsfrb_status gemm_nt_g(int64_t M, int N, int K, const bf16 *A, const bf16 *B, float *C, gemm::Gather gx,
+                       cudaStream_t s) {
     if (N <= 32) {
         const dim3 g2(static_cast<unsigned>((M + 127) / 128), static_cast<unsigned>((N + 31) / 32), 1);
-        gemm::gemm_kernel<128, 32, false><<<g2, gemm::kThreads, 0, s>>>(static_cast<int>(M), N, K, A, K, B, K, C, N, 1);
+        gemm::gemm_kernel<128, 32, false, G>
+            <<<g2, gemm::kThreads, 0, s>>>(static_cast<int>(M), N, K, A, K, B, K, C, N, 1, gx);
     } else {
-        gemm::gemm_kernel<128, 64, false><<<grid, gemm::kThreads, 0, s>>>(static_cast<int>(M), N, K, A, K, B, K, C, N, 1);
+        const dim3 grid(static_cast<unsigned>((M + 127) / 128), static_cast<unsigned>((N + 63) / 64), 1);
+        gemm::gemm_kernel<128, 64, false, G>
+            <<<grid, gemm::kThreads, 0, s>>>(static_cast<int>(M), N, K, A, K, B, K, C, N, 1, gx);
     }
     return cudaGetLastError() == cudaSuccess ? NSFRB_OK : NSFRB_ECUDA;
 }
 
-// C[M][N] (zeroed here) = A[K][M]^T B[K][N] with split-K over K.
-nsfrb_status gemm_tn(int M, int N, int64_t K, const bf16 *A, const bf16 *B, float *C, cudaStream_t s) {
+// C[M][N] (zeroed here) = A[K][M]^T B[K][N] with split-K over K; with gx.x set, B is the
+// im2col matrix of gx (gathered).
+template <int G>
+nsfrb_status gemm_tn_g(int M, int N, int64_t K, const bf16 *A, const bf16 *B, float *C, gemm::Gather gx,
+                       cudaStream_t s) {
     if (cudaMemsetAsync(C, 0, sizeof(float) * static_cast<size_t>(M) * N, s) != cudaSuccess) return NSFRB_ECUDA;
     const int mt = (M + 127) / 128, nt = (N + 63) / 64;
     const int64_t k_steps = (K + gemm::BK - 1) / gemm::BK;
     int split = static_cast<int>(std::min<int64_t>(k_steps, std::max<int64_t>(1, 4 * 152 / (mt * nt))));
     split = std::max(split, 1);
-    gemm::gemm_kernel<128, 64, true><<<dim3(mt, nt, split), gemm::kThreads, 0, s>>>(
-        M, N, static_cast<int>(K), A, M, B, N, C, N, split);
+    gemm::gemm_kernel<128, 64, true, G><<<dim3(mt, nt, split), gemm::kThreads, 0, s>>>(
+        M, N, static_cast<int>(K), A, M, B, N, C, N, split, gx);
     return cudaGetLastError() == cudaSuccess ? NSFRB_OK : NSFRB_ECUDA;
+}
+
+nsfrb_status gemm_nt(int64_t M, int N, int K, const bf16 *A, const bf16 *B, float *C, cudaStream_t s) {
+    return gemm_nt_g<0>(M, N, K, A, B, C, gemm::Gather{}, s);
+}
+nsfrb_status gemm_tn(int M, int N, int64_t K, const bf16 *A, const bf16 *B, float *C, cudaStream_t s) {
+    return gemm_tn_g<0>(M, N, K, A, B, C, gemm::Gather{}, s);
 }
 
 // Forward of the conv blocks and the head; keeps everything the backward needs.
@@ -529,8 +521,7 @@ nsfrb_status forward(nsfrb_clf_s *c, const bf16 *x, const float *labels, int B, 
     for (int l = 0; l < 4; ++l) {
         const int D = c->dims[l][0], H = c->dims[l][1], W = c->dims[l][2], Ci = c->dims[l][3], Co = cf.c[l];
         const int64_t P = static_cast<int64_t>(B) * D * H * W;
-        im2col3d_kernel<<<grid_for(P * 27 * Ci / 8), kTB, 0, s>>>(in, c->col, B, D, H, W, Ci);
-        if (gemm_nt(P, Co, 27 * Ci, c->col, c->wb[l], c->y[l], s) != NSFRB_OK)
+        if (gemm_nt_g<1>(P, Co, 27 * Ci, nullptr, c->wb[l], c->y[l], gemm::Gather{in, D, H, W, Ci}, s) != NSFRB_OK)
             return clf_cuda(c, cudaGetLastError(), "conv gemm");
         if (train) {
             const int nblk = static_cast<int>((P + kPartRows - 1) / kPartRows);
@@ -583,15 +574,15 @@ nsfrb_status backward(nsfrb_clf_s *c, const bf16 *x, const float *labels, int B,
         bn_bwd_apply_kernel<<<grid_for(P * Co), kTB, 0, s>>>(c->dz, c->y[l], c->mean[l], c->rstd[l],
                                                              c->params + c->off_g[l], c->grads + c->off_g[l],
                                                              c->grads + c->off_b[l], P, Co, c->dyb);
-        // weight gradient: dW[co][(k, ci)] = sum_p dy[p][co] col[p][(k, ci)]
+        // weight gradient: dW[co][(k, ci)] = sum_p dy[p][co] col[p][(k, ci)], col gathered from the input
         const bf16 *in = (l == 0) ? x : c->act[l];
-        im2col3d_kernel<<<grid_for(P * 27 * Ci / 8), kTB, 0, s>>>(in, c->col, B, D, H, W, Ci);
-        if (gemm_tn(Co, 27 * Ci, P, c->dyb, c->col, c->grads + c->off_w[l], s) != NSFRB_OK)
+        if (gemm_tn_g<2>(Co, 27 * Ci, P, c->dyb, nullptr, c->grads + c->off_w[l], gemm::Gather{in, D, H, W, Ci}, s) !=
+            NSFRB_OK)
             return clf_cuda(c, cudaGetLastError(), "weight gemm");
         if (l > 0) {
             // input gradient: a convolution of dy with the flipped, transposed weights
-            im2col3d_kernel<<<grid_for(P * 27 * Co / 8), kTB, 0, s>>>(c->dyb, c->col, B, D, H, W, Co);
-            if (gemm_nt(P, Ci, 27 * Co, c->col, c->wf[l], c->dact, s) != NSFRB_OK)
+            if (gemm_nt_g<1>(P, Ci, 27 * Co, nullptr, c->wf[l], c->dact, gemm::Gather{c->dyb, D, H, W, Co}, s) !=
+                NSFRB_OK)
                 return clf_cuda(c, cudaGetLastError(), "input gemm");
         }
     }
@@ -647,10 +638,9 @@ nsfrb_status nsfrb_clf_create(const nsfrb_clf_config *cfg, nsfrb_clf_t *out) {
     m->n_params = o;
 
     const int B = c.batch;
-    int64_t col = 0, zmax = 0, dact = static_cast<int64_t>(B) * m->Fin, part = 0;
+    int64_t zmax = 0, dact = static_cast<int64_t>(B) * m->Fin, part = 0;
     for (int l = 0; l < 4; ++l) {
         const int64_t P = static_cast<int64_t>(B) * m->dims[l][0] * m->dims[l][1] * m->dims[l][2];
-        col = std::max(col, P * 27 * std::max(m->dims[l][3], c.c[l]));
         zmax = std::max(zmax, P * c.c[l]);
         dact = std::max(dact, P * m->dims[l][3]);
         part = std::max(part, ((P + kPartRows - 1) / kPartRows) * 2 * c.c[l]);
@@ -678,7 +668,6 @@ nsfrb_status nsfrb_clf_create(const nsfrb_clf_config *cfg, nsfrb_clf_t *out) {
         A(reinterpret_cast<void **>(&m->mean[l]), sizeof(float) * c.c[l]);
         A(reinterpret_cast<void **>(&m->rstd[l]), sizeof(float) * c.c[l]);
     }
-    A(reinterpret_cast<void **>(&m->col), sizeof(bf16) * col);
     A(reinterpret_cast<void **>(&m->dyb), sizeof(bf16) * zmax);
     A(reinterpret_cast<void **>(&m->dz), sizeof(float) * zmax);
     A(reinterpret_cast<void **>(&m->dact), sizeof(float) * dact);
@@ -893,7 +882,7 @@ nsfrb_status nsfrb_clf_load(nsfrb_clf_t clf, const char *path) {
 void nsfrb_clf_destroy(nsfrb_clf_t clf) {
     if (!clf) return;
     cudaDeviceSynchronize();
-    void *ptrs[] = {clf->params, clf->grads, clf->adam_m, clf->adam_v, clf->run_mean, clf->run_var, clf->col,
+    void *ptrs[] = {clf->params, clf->grads, clf->adam_m, clf->adam_v, clf->run_mean, clf->run_var,
                     clf->dyb, clf->dz, clf->dact, clf->part, clf->feat, clf->h1, clf->h1d, clf->dh1, clf->logit,
                     clf->loss_terms, clf->loss};
     for (void *p : ptrs) cudaFree(p);

@@ -9,6 +9,13 @@
 // (zero-filled outside the matrix, double buffered) and fed to
 // mma.m16n8k16 through ldmatrix (.trans for the TN layout).  K must be a
 // multiple of 8 and every row start 16-byte aligned.
+//
+// Implicit convolution (G = 1, 2): the im2col matrix of a channels-last volume
+// x[b][z][y][x][c] (3x3x3 taps, zero padding 1, column index tap * C + c with
+// tap = (dz * 3 + dy) * 3 + dx) is never stored: the tile loader gathers its 16-byte
+// chunks (8 channels of one tap) straight from x, zero-filling taps outside the
+// volume.  G = 1 gathers the A rows of an NT product (conv forward / input gradient),
+// G = 2 the B operand of a TN product (weight gradient).  C must be a multiple of 8.
 #pragma once
 
 #include <cstdint>
@@ -57,6 +64,11 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
 
 // TRANS = false: A tile stored [BM][BK+8], B tile [BN][BK+8] (K contiguous)
 // TRANS = true:  A tile stored [BK][BM+8], B tile [BK][BN+8] (M / N contiguous)
+struct Gather {
+    const __nv_bfloat16 *x;   // [B][D][H][W][C]
+    int D, H, W, C;
+};
+
 template <int BM, int BN, bool TRANS>
 struct Smem {
     static constexpr int A_ELEMS = TRANS ? BK * (BM + 8) : BM * (BK + 8);
@@ -66,11 +78,12 @@ struct Smem {
 };
 
 // One CTA computes a BM x BN tile of C over the K range [k_lo, k_hi).
-template <int BM, int BN, bool TRANS>
+template <int BM, int BN, bool TRANS, int G = 0>
 __global__ void __launch_bounds__(kThreads) gemm_kernel(int M, int N, int K, const __nv_bfloat16 *__restrict__ A,
                                                         int64_t lda, const __nv_bfloat16 *__restrict__ B,
                                                         int64_t ldb, float *__restrict__ C, int64_t ldc,
-                                                        int k_split) {
+                                                        int k_split, Gather gx) {
+    static_assert(G == 0 || (G == 1 && !TRANS) || (G == 2 && TRANS), "gather mode / layout mismatch");
     constexpr int WM = (BN >= 64) ? 2 : 4;    // warps along M
     constexpr int WN = 4 / WM;                // warps along N
     constexpr int TM = BM / WM, TN = BN / WN; // warp tile
@@ -87,9 +100,52 @@ __global__ void __launch_bounds__(kThreads) gemm_kernel(int M, int N, int K, con
     const int ks0 = blockIdx.z * per, ks1 = min(k_steps, ks0 + per);
     if (ks0 >= ks1) return;
 
+    // G = 1: the voxels of this thread's A rows (rows tid/4 + 32 j, chunk column (tid % 4) * 8)
+    constexpr int kRowsPer = (G == 1) ? BM * (BK / 8) / kThreads : 1;
+    int64_t g_base[kRowsPer];
+    int g_z[kRowsPer], g_y[kRowsPer], g_x[kRowsPer];
+    if constexpr (G == 1) {
+#pragma unroll
+        for (int j = 0; j < kRowsPer; ++j) {
+            const int gm = m0 + (tid + kThreads * j) / (BK / 8);
+            const int v = gm < M ? gm : 0;
+            g_x[j] = v % gx.W;
+            g_y[j] = (v / gx.W) % gx.H;
+            g_z[j] = (v / (gx.W * gx.H)) % gx.D;
+            g_base[j] = gm < M ? static_cast<int64_t>(v / (gx.W * gx.H * gx.D)) * gx.D * gx.H * gx.W : -1;
+        }
+    }
+    // G = 2: the tap and channel of this thread's B chunk column (n0 + (tid % 8) * 8)
+    int g_dz = 0, g_dy = 0, g_dx = 0, g_ci = 0;
+    bool g_nok = false;
+    if constexpr (G == 2) {
+        const int gn = n0 + (tid % (BN / 8)) * 8;
+        g_nok = gn < N;
+        const int tap = (g_nok ? gn : 0) / gx.C;
+        g_ci = (g_nok ? gn : 0) - tap * gx.C;
+        g_dz = tap / 9;
+        g_dy = (tap / 3) % 3;
+        g_dx = tap % 3;
+    }
+
     auto load_tile = [&](int stage, int ks) {
         const int kb = ks * BK;
-        if (!TRANS) {
+        if constexpr (G == 1) {
+            const int kc = (tid % (BK / 8)) * 8, gk = kb + kc;
+            const bool kok = gk < K;
+            const int tap = kok ? gk / gx.C : 0, ci = kok ? gk - tap * gx.C : 0;
+            const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+#pragma unroll
+            for (int j = 0; j < kRowsPer; ++j) {
+                const int r = (tid + kThreads * j) / (BK / 8);
+                const int zz = g_z[j] + dz, yy = g_y[j] + dy, xx = g_x[j] + dx;
+                const bool ok = kok && g_base[j] >= 0 && zz >= 0 && zz < gx.D && yy >= 0 && yy < gx.H && xx >= 0 &&
+                                xx < gx.W;
+                const __nv_bfloat16 *src =
+                    ok ? gx.x + (g_base[j] + (static_cast<int64_t>(zz) * gx.H + yy) * gx.W + xx) * gx.C + ci : gx.x;
+                cp_async16(&sm.a[stage][r * (BK + 8) + kc], src, ok);
+            }
+        } else if constexpr (!TRANS) {
             // A: BM rows x 4 chunks of 8 along K
             for (int c = tid; c < BM * (BK / 8); c += kThreads) {
                 const int r = c / (BK / 8), kc = (c % (BK / 8)) * 8;
@@ -97,6 +153,8 @@ __global__ void __launch_bounds__(kThreads) gemm_kernel(int M, int N, int K, con
                 const bool ok = gm < M && gk < K;
                 cp_async16(&sm.a[stage][r * (BK + 8) + kc], ok ? A + gm * lda + gk : A, ok);
             }
+        }
+        if constexpr (!TRANS) {
             for (int c = tid; c < BN * (BK / 8); c += kThreads) {
                 const int r = c / (BK / 8), kc = (c % (BK / 8)) * 8;
                 const int gn = n0 + r, gk = kb + kc;
@@ -111,11 +169,28 @@ __global__ void __launch_bounds__(kThreads) gemm_kernel(int M, int N, int K, con
                 const bool ok = gk < K && gm < M;
                 cp_async16(&sm.a[stage][r * (BM + 8) + mc], ok ? A + gk * lda + gm : A, ok);
             }
-            for (int c = tid; c < BK * (BN / 8); c += kThreads) {
-                const int r = c / (BN / 8), nc = (c % (BN / 8)) * 8;
-                const int gk = kb + r, gn = n0 + nc;
-                const bool ok = gk < K && gn < N;
-                cp_async16(&sm.b[stage][r * (BN + 8) + nc], ok ? B + gk * ldb + gn : B, ok);
+            if constexpr (G == 2) {
+                // B rows are voxels p = gk; this thread's columns are one tap's 8 channels
+                for (int c = tid; c < BK * (BN / 8); c += kThreads) {
+                    const int r = c / (BN / 8), nc = (c % (BN / 8)) * 8;
+                    const int gk = kb + r;
+                    const int v = gk < K ? gk : 0;
+                    const int xx = v % gx.W + g_dx - 1, yy = (v / gx.W) % gx.H + g_dy - 1;
+                    const int zz = (v / (gx.W * gx.H)) % gx.D + g_dz - 1, bb = v / (gx.W * gx.H * gx.D);
+                    const bool ok = gk < K && g_nok && zz >= 0 && zz < gx.D && yy >= 0 && yy < gx.H && xx >= 0 &&
+                                    xx < gx.W;
+                    const __nv_bfloat16 *src =
+                        ok ? gx.x + ((((static_cast<int64_t>(bb) * gx.D + zz) * gx.H + yy) * gx.W + xx) * gx.C + g_ci)
+                           : gx.x;
+                    cp_async16(&sm.b[stage][r * (BN + 8) + nc], src, ok);
+                }
+            } else {
+                for (int c = tid; c < BK * (BN / 8); c += kThreads) {
+                    const int r = c / (BN / 8), nc = (c % (BN / 8)) * 8;
+                    const int gk = kb + r, gn = n0 + nc;
+                    const bool ok = gk < K && gn < N;
+                    cp_async16(&sm.b[stage][r * (BN + 8) + nc], ok ? B + gk * ldb + gn : B, ok);
+                }
             }
         }
         cp_async_commit();
