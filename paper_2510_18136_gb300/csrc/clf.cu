@@ -74,16 +74,41 @@ __global__ void bn_partial_kernel(const float *__restrict__ y, int64_t P, int C,
 }
 
 // Final reduction in FP64: mean, rstd (biased variance), running statistics.
-__global__ void bn_finish_kernel(const float *__restrict__ part, int nblk, int C, int64_t P, float eps,
-                                 float momentum, int update_running, float *__restrict__ mean,
-                                 float *__restrict__ rstd, float *__restrict__ run_mean, float *__restrict__ run_var) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= C) return;
-    double s = 0.0, q = 0.0;
-    for (int b = 0; b < nblk; ++b) {
-        s += part[static_cast<int64_t>(b) * 2 * C + c];
-        q += part[static_cast<int64_t>(b) * 2 * C + C + c];
+// Per channel c (one CTA of kFinThreads): the sums over the nblk block partials of part[b][0][c]
+// and part[b][1][c] in FP64, as thread-strided sums followed by a fixed shared-memory tree
+// (the same order every run).
+constexpr int kFinThreads = 256;
+__device__ __forceinline__ void channel_sums(const float *__restrict__ part, int nblk, int C, int c, double &s,
+                                             double &q) {
+    __shared__ double sh[2][kFinThreads];
+    double a = 0.0, b2 = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += kFinThreads) {
+        a += part[static_cast<int64_t>(b) * 2 * C + c];
+        b2 += part[static_cast<int64_t>(b) * 2 * C + C + c];
     }
+    sh[0][threadIdx.x] = a;
+    sh[1][threadIdx.x] = b2;
+    __syncthreads();
+    for (int o = kFinThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + o];
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    s = sh[0][0];
+    q = sh[1][0];
+}
+
+__global__ void __launch_bounds__(kFinThreads) bn_finish_kernel(const float *__restrict__ part, int nblk, int C,
+                                                                int64_t P, float eps, float momentum,
+                                                                int update_running, float *__restrict__ mean,
+                                                                float *__restrict__ rstd, float *__restrict__ run_mean,
+                                                                float *__restrict__ run_var) {
+    const int c = blockIdx.x;
+    double s, q;
+    channel_sums(part, nblk, C, c, s, q);
+    if (threadIdx.x != 0) return;
     const double mu = s / static_cast<double>(P);
     double var = q / static_cast<double>(P) - mu * mu;
     if (var < 0.0) var = 0.0;
@@ -191,15 +216,13 @@ __global__ void bn_bwd_partial_kernel(const float *__restrict__ dz, const float 
 }
 
 // dbeta = sum dz, dgamma = sum dz * yhat (written into the gradient vector).
-__global__ void bn_bwd_finish_kernel(const float *__restrict__ part, int nblk, int C, float *__restrict__ dgamma,
-                                     float *__restrict__ dbeta) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= C) return;
-    double s = 0.0, q = 0.0;
-    for (int b = 0; b < nblk; ++b) {
-        s += part[static_cast<int64_t>(b) * 2 * C + c];
-        q += part[static_cast<int64_t>(b) * 2 * C + C + c];
-    }
+__global__ void __launch_bounds__(kFinThreads) bn_bwd_finish_kernel(const float *__restrict__ part, int nblk, int C,
+                                                                    float *__restrict__ dgamma,
+                                                                    float *__restrict__ dbeta) {
+    const int c = blockIdx.x;
+    double s, q;
+    channel_sums(part, nblk, C, c, s, q);
+    if (threadIdx.x != 0) return;
     dbeta[c] = static_cast<float>(s);
     dgamma[c] = static_cast<float>(q);
 }
@@ -497,12 +520,22 @@ template <int G>
 nsfrb_status gemm_tn_g(int M, int N, int64_t K, const bf16 *A, const bf16 *B, float *C, gemm::Gather gx,
                        cudaStream_t s) {
     if (cudaMemsetAsync(C, 0, sizeof(float) * static_cast<size_t>(M) * N, s) != cudaSuccess) return NSFRB_ECUDA;
-    const int mt = (M + 127) / 128, nt = (N + 63) / 64;
+    // tile rows follow M (the output channels: 32 or 64 in the network), wide tiles along N
+    const int bm = M <= 32 ? 32 : (M <= 64 ? 64 : 128), bn = bm == 128 ? 64 : 128;
+    const int mt = (M + bm - 1) / bm, nt = (N + bn - 1) / bn;
     const int64_t k_steps = (K + gemm::BK - 1) / gemm::BK;
     int split = static_cast<int>(std::min<int64_t>(k_steps, std::max<int64_t>(1, 4 * 152 / (mt * nt))));
     split = std::max(split, 1);
-    gemm::gemm_kernel<128, 64, true, G><<<dim3(mt, nt, split), gemm::kThreads, 0, s>>>(
-        M, N, static_cast<int>(K), A, M, B, N, C, N, split, gx);
+    const dim3 grid(mt, nt, split);
+    if (bm == 32)
+        gemm::gemm_kernel<32, 128, true, G><<<grid, gemm::kThreads, 0, s>>>(M, N, static_cast<int>(K), A, M, B, N, C,
+                                                                             N, split, gx);
+    else if (bm == 64)
+        gemm::gemm_kernel<64, 128, true, G><<<grid, gemm::kThreads, 0, s>>>(M, N, static_cast<int>(K), A, M, B, N, C,
+                                                                             N, split, gx);
+    else
+        gemm::gemm_kernel<128, 64, true, G><<<grid, gemm::kThreads, 0, s>>>(M, N, static_cast<int>(K), A, M, B, N, C,
+                                                                             N, split, gx);
     return cudaGetLastError() == cudaSuccess ? NSFRB_OK : NSFRB_ECUDA;
 }
 
@@ -526,8 +559,8 @@ nsfrb_status forward(nsfrb_clf_s *c, const bf16 *x, const float *labels, int B, 
         if (train) {
             const int nblk = static_cast<int>((P + kPartRows - 1) / kPartRows);
             bn_partial_kernel<<<nblk, kTB, 2 * Co * sizeof(float), s>>>(c->y[l], P, Co, kPartRows, c->part);
-            bn_finish_kernel<<<(Co + 63) / 64, 64, 0, s>>>(c->part, nblk, Co, P, 1e-5f, cf.bn_momentum, 1, c->mean[l],
-                                                           c->rstd[l], c->run_mean + rs, c->run_var + rs);
+            bn_finish_kernel<<<Co, kFinThreads, 0, s>>>(c->part, nblk, Co, P, 1e-5f, cf.bn_momentum, 1, c->mean[l],
+                                                        c->rstd[l], c->run_mean + rs, c->run_var + rs);
         } else {
             bn_eval_kernel<<<(Co + 63) / 64, 64, 0, s>>>(c->run_mean + rs, c->run_var + rs, Co, 1e-5f, c->mean[l],
                                                          c->rstd[l]);
@@ -569,8 +602,8 @@ nsfrb_status backward(nsfrb_clf_s *c, const bf16 *x, const float *labels, int B,
         const int nblk = static_cast<int>((P + kPartRows - 1) / kPartRows);
         bn_bwd_partial_kernel<<<nblk, kTB, 2 * Co * sizeof(float), s>>>(c->dz, c->y[l], c->mean[l], c->rstd[l], P, Co,
                                                                         kPartRows, c->part);
-        bn_bwd_finish_kernel<<<(Co + 63) / 64, 64, 0, s>>>(c->part, nblk, Co, c->grads + c->off_g[l],
-                                                           c->grads + c->off_b[l]);
+        bn_bwd_finish_kernel<<<Co, kFinThreads, 0, s>>>(c->part, nblk, Co, c->grads + c->off_g[l],
+                                                        c->grads + c->off_b[l]);
         bn_bwd_apply_kernel<<<grid_for(P * Co), kTB, 0, s>>>(c->dz, c->y[l], c->mean[l], c->rstd[l],
                                                              c->params + c->off_g[l], c->grads + c->off_g[l],
                                                              c->grads + c->off_b[l], P, Co, c->dyb);
