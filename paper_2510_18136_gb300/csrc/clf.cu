@@ -554,7 +554,7 @@ nsfrb_status forward(nsfrb_clf_s *c, const bf16 *x, const float *labels, int B, 
     for (int l = 0; l < 4; ++l) {
         const int D = c->dims[l][0], H = c->dims[l][1], W = c->dims[l][2], Ci = c->dims[l][3], Co = cf.c[l];
         const int64_t P = static_cast<int64_t>(B) * D * H * W;
-        if (gemm_nt_g<1>(P, Co, 27 * Ci, nullptr, c->wb[l], c->y[l], gemm::Gather{in, D, H, W, Ci}, s) != NSFRB_OK)
+        if (gemm_nt_g<1>(P, Co, 27 * Ci, nullptr, c->wb[l], c->y[l], gemm::make_gather(in, D, H, W, Ci), s) != NSFRB_OK)
             return clf_cuda(c, cudaGetLastError(), "conv gemm");
         if (train) {
             const int nblk = static_cast<int>((P + kPartRows - 1) / kPartRows);
@@ -609,12 +609,12 @@ nsfrb_status backward(nsfrb_clf_s *c, const bf16 *x, const float *labels, int B,
                                                              c->grads + c->off_b[l], P, Co, c->dyb);
         // weight gradient: dW[co][(k, ci)] = sum_p dy[p][co] col[p][(k, ci)], col gathered from the input
         const bf16 *in = (l == 0) ? x : c->act[l];
-        if (gemm_tn_g<2>(Co, 27 * Ci, P, c->dyb, nullptr, c->grads + c->off_w[l], gemm::Gather{in, D, H, W, Ci}, s) !=
+        if (gemm_tn_g<2>(Co, 27 * Ci, P, c->dyb, nullptr, c->grads + c->off_w[l], gemm::make_gather(in, D, H, W, Ci), s) !=
             NSFRB_OK)
             return clf_cuda(c, cudaGetLastError(), "weight gemm");
         if (l > 0) {
             // input gradient: a convolution of dy with the flipped, transposed weights
-            if (gemm_nt_g<1>(P, Ci, 27 * Co, nullptr, c->wf[l], c->dact, gemm::Gather{c->dyb, D, H, W, Co}, s) !=
+            if (gemm_nt_g<1>(P, Ci, 27 * Co, nullptr, c->wf[l], c->dact, gemm::make_gather(c->dyb, D, H, W, Co), s) !=
                 NSFRB_OK)
                 return clf_cuda(c, cudaGetLastError(), "input gemm");
         }

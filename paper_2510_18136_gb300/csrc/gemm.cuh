@@ -64,10 +64,42 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
 
 // TRANS = false: A tile stored [BM][BK+8], B tile [BN][BK+8] (K contiguous)
 // TRANS = true:  A tile stored [BK][BM+8], B tile [BK][BN+8] (M / N contiguous)
+// Division by an invariant divisor d for 0 <= n < 2^31 (Granlund and Montgomery,
+// "Division by invariant integers using multiplication", 1994, round-up variant):
+// l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1, n / d = (umulhi(n, m) + n) >> l.
+struct FastDiv {
+    uint32_t m = 1, l = 0;
+};
+inline FastDiv make_fastdiv(uint32_t d) {
+    FastDiv f;
+    uint32_t l = 0;
+    while ((uint64_t(1) << l) < d) ++l;
+    f.l = l;
+    f.m = static_cast<uint32_t>(((uint64_t(1) << 32) * ((uint64_t(1) << l) - d)) / d + 1);
+    return f;
+}
+__device__ __forceinline__ int fdiv(int n, FastDiv f) {
+    return static_cast<int>((__umulhi(static_cast<uint32_t>(n), f.m) + static_cast<uint32_t>(n)) >> f.l);
+}
+
 struct Gather {
     const __nv_bfloat16 *x;   // [B][D][H][W][C]
     int D, H, W, C;
+    FastDiv fD, fH, fW, fC;
 };
+inline Gather make_gather(const __nv_bfloat16 *x, int D, int H, int W, int C) {
+    Gather g;
+    g.x = x;
+    g.D = D;
+    g.H = H;
+    g.W = W;
+    g.C = C;
+    g.fD = make_fastdiv(D);
+    g.fH = make_fastdiv(H);
+    g.fW = make_fastdiv(W);
+    g.fC = make_fastdiv(C);
+    return g;
+}
 
 template <int BM, int BN, bool TRANS>
 struct Smem {
@@ -115,17 +147,23 @@ __global__ void __launch_bounds__(kThreads) gemm_kernel(int M, int N, int K, con
             g_base[j] = gm < M ? static_cast<int64_t>(v / (gx.W * gx.H * gx.D)) * gx.D * gx.H * gx.W : -1;
         }
     }
-    // G = 2: the tap and channel of this thread's B chunk column (n0 + (tid % 8) * 8)
-    int g_dz = 0, g_dy = 0, g_dx = 0, g_ci = 0;
-    bool g_nok = false;
+    // G = 2: each thread loads kCPT consecutive chunks of one B row (one voxel); the taps and
+    // channels of its chunk columns are fixed for the whole K loop
+    constexpr int kCPT = (G == 2) ? BK * (BN / 8) / kThreads : 1;
+    static_assert(G != 2 || (BN / 8) % kCPT == 0, "a thread's chunks must lie in one row");
+    int g_dz[kCPT], g_dy[kCPT], g_dx[kCPT], g_ci[kCPT];
+    bool g_nok[kCPT];
     if constexpr (G == 2) {
-        const int gn = n0 + (tid % (BN / 8)) * 8;
-        g_nok = gn < N;
-        const int tap = (g_nok ? gn : 0) / gx.C;
-        g_ci = (g_nok ? gn : 0) - tap * gx.C;
-        g_dz = tap / 9;
-        g_dy = (tap / 3) % 3;
-        g_dx = tap % 3;
+#pragma unroll
+        for (int j = 0; j < kCPT; ++j) {
+            const int gn = n0 + ((tid * kCPT + j) % (BN / 8)) * 8;
+            g_nok[j] = gn < N;
+            const int tap = fdiv(g_nok[j] ? gn : 0, gx.fC);
+            g_ci[j] = (g_nok[j] ? gn : 0) - tap * gx.C;
+            g_dz[j] = tap / 9 - 1;
+            g_dy[j] = (tap / 3) % 3 - 1;
+            g_dx[j] = tap % 3 - 1;
+        }
     }
 
     auto load_tile = [&](int stage, int ks) {
@@ -133,7 +171,7 @@ __global__ void __launch_bounds__(kThreads) gemm_kernel(int M, int N, int K, con
         if constexpr (G == 1) {
             const int kc = (tid % (BK / 8)) * 8, gk = kb + kc;
             const bool kok = gk < K;
-            const int tap = kok ? gk / gx.C : 0, ci = kok ? gk - tap * gx.C : 0;
+            const int tap = kok ? fdiv(gk, gx.fC) : 0, ci = kok ? gk - tap * gx.C : 0;
             const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
 #pragma unroll
             for (int j = 0; j < kRowsPer; ++j) {
@@ -170,17 +208,22 @@ __global__ void __launch_bounds__(kThreads) gemm_kernel(int M, int N, int K, con
                 cp_async16(&sm.a[stage][r * (BM + 8) + mc], ok ? A + gk * lda + gm : A, ok);
             }
             if constexpr (G == 2) {
-                // B rows are voxels p = gk; this thread's columns are one tap's 8 channels
-                for (int c = tid; c < BK * (BN / 8); c += kThreads) {
-                    const int r = c / (BN / 8), nc = (c % (BN / 8)) * 8;
-                    const int gk = kb + r;
-                    const int v = gk < K ? gk : 0;
-                    const int xx = v % gx.W + g_dx - 1, yy = (v / gx.W) % gx.H + g_dy - 1;
-                    const int zz = (v / (gx.W * gx.H)) % gx.D + g_dz - 1, bb = v / (gx.W * gx.H * gx.D);
-                    const bool ok = gk < K && g_nok && zz >= 0 && zz < gx.D && yy >= 0 && yy < gx.H && xx >= 0 &&
+                // B row r is the voxel p = kb + r, decomposed once for the thread's kCPT chunks
+                const int r = (tid * kCPT) / (BN / 8);
+                const int gk = kb + r;
+                const bool kok = gk < K;
+                const int v = kok ? gk : 0;
+                const int t1 = fdiv(v, gx.fW), t2 = fdiv(t1, gx.fH), bb = fdiv(t2, gx.fD);
+                const int x0 = v - t1 * gx.W, y0 = t1 - t2 * gx.H, z0 = t2 - bb * gx.D;
+#pragma unroll
+                for (int j = 0; j < kCPT; ++j) {
+                    const int nc = ((tid * kCPT + j) % (BN / 8)) * 8;
+                    const int xx = x0 + g_dx[j], yy = y0 + g_dy[j], zz = z0 + g_dz[j];
+                    const bool ok = kok && g_nok[j] && zz >= 0 && zz < gx.D && yy >= 0 && yy < gx.H && xx >= 0 &&
                                     xx < gx.W;
                     const __nv_bfloat16 *src =
-                        ok ? gx.x + ((((static_cast<int64_t>(bb) * gx.D + zz) * gx.H + yy) * gx.W + xx) * gx.C + g_ci)
+                        ok ? gx.x + ((((static_cast<int64_t>(bb) * gx.D + zz) * gx.H + yy) * gx.W + xx) * gx.C +
+                                     g_ci[j])
                            : gx.x;
                     cp_async16(&sm.b[stage][r * (BN + 8) + nc], src, ok);
                 }
