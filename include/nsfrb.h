@@ -350,7 +350,7 @@ typedef struct {
     int32_t batch;          /* largest batch per call                              */
     int32_t d, h, w;        /* cutout time samples, rows, columns (multiples of 16) */
     int32_t c0;             /* subbands = input channels (multiple of 8)            */
-    int32_t c[4];           /* channels of the four conv blocks (multiples of 8)    */
+    int32_t c[4];           /* channels of the four conv blocks (multiples of 8, <= 256) */
     int32_t f;              /* hidden units of the head (1..1024)                   */
     float dropout;          /* dropout rate of the hidden units, [0, 1)             */
     uint64_t seed;          /* dropout key                                          */

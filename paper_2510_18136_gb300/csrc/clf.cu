@@ -48,30 +48,6 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
 
 // ------------------------------------------------------------------ kernels
 
-// Per-block partial sums of y[p][c] and y^2 over rows (FP32 within a block).
-__global__ void bn_partial_kernel(const float *__restrict__ y, int64_t P, int C, int rows_per_block,
-                                  float *__restrict__ part) {
-    extern __shared__ float sh[];   // [2][C]
-    for (int c = threadIdx.x; c < 2 * C; c += blockDim.x) sh[c] = 0.0f;
-    __syncthreads();
-    const int64_t r0 = static_cast<int64_t>(blockIdx.x) * rows_per_block;
-    const int64_t r1 = min(P, r0 + rows_per_block);
-    // thread t handles channel t % C for rows r0 + t / C, stepping blockDim / C rows
-    const int c = threadIdx.x % C, lanes = blockDim.x / C, ro = threadIdx.x / C;
-    float s = 0.0f, q = 0.0f;
-    if (ro < lanes)
-        for (int64_t r = r0 + ro; r < r1; r += lanes) {
-            const float v = y[r * C + c];
-            s += v;
-            q += v * v;
-        }
-    if (ro < lanes) {
-        atomicAdd(&sh[c], s);
-        atomicAdd(&sh[C + c], q);
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < 2 * C; i += blockDim.x) part[static_cast<int64_t>(blockIdx.x) * 2 * C + i] = sh[i];
-}
 
 // Final reduction in FP64: mean, rstd (biased variance), running statistics.
 // Per channel c (one CTA of kFinThreads): the sums over the nblk block partials of part[b][0][c]
@@ -121,6 +97,99 @@ __global__ void __launch_bounds__(kFinThreads) bn_finish_kernel(const float *__r
     }
 }
 
+// Backward of max-pool, ReLU and batch norm over pooling windows.  The gradient at the
+// batch-norm output, dz, is dpool at the window's arg-max voxel when the pre-ReLU value
+// there is positive, else 0; it is recomputed here from (dpool, arg, y) rather than stored.
+// Window w of the pooled volume [B][D/2][H/2][W/2] and its voxel q (dz, dy, dx bits).
+struct PoolGeom {
+    int D, H, W, C;
+    gemm::FastDiv fW2, fH2, fD2;
+};
+
+__device__ __forceinline__ int64_t window_voxel(int64_t w, int q, const PoolGeom &g) {
+    const int W2 = g.W / 2, H2 = g.H / 2, D2 = g.D / 2;
+    const int wi = static_cast<int>(w);
+    const int t1 = gemm::fdiv(wi, g.fW2), t2 = gemm::fdiv(t1, g.fH2), b = gemm::fdiv(t2, g.fD2);
+    const int x2 = wi - t1 * W2, y2 = t1 - t2 * H2, z2 = t2 - b * D2;
+    return ((static_cast<int64_t>(b) * g.D + 2 * z2 + (q >> 2)) * g.H + 2 * y2 + ((q >> 1) & 1)) * g.W + 2 * x2 +
+           (q & 1);
+}
+
+// Per-block partial sums over windows [blockIdx.x * wpb, ...) of dz and dz * yhat per channel
+// (only the arg-max voxel of a window can carry dz), reduced over the block's threads in a
+// fixed order: part[block][0][c], part[block][1][c].
+__global__ void __launch_bounds__(kTB) bn_bwd_pool_partial_kernel(const float *__restrict__ dpool,
+                                                                  const uint8_t *__restrict__ arg,
+                                                                  const float *__restrict__ y,
+                                                                  const float *__restrict__ mean,
+                                                                  const float *__restrict__ rstd,
+                                                                  const float *__restrict__ gamma,
+                                                                  const float *__restrict__ beta, int64_t n_win,
+                                                                  int wpb, PoolGeom pg, float *__restrict__ part) {
+    __shared__ float sh[2][kTB];
+    const int C = pg.C;
+    const int c = threadIdx.x % C, lanes = kTB / C, ro = threadIdx.x / C;
+    float s = 0.0f, q = 0.0f;
+    if (ro < lanes) {
+        const float mu = mean[c], rs = rstd[c], ga = gamma[c], be = beta[c];
+        const int64_t w0 = static_cast<int64_t>(blockIdx.x) * wpb, w1 = min(n_win, w0 + wpb);
+        for (int64_t w = w0 + ro; w < w1; w += lanes) {
+            const int64_t i = w * C + c;
+            const int a = arg[i];
+            const float yh = (y[window_voxel(w, a, pg) * C + c] - mu) * rs;
+            const float dzv = (ga * yh + be > 0.0f) ? dpool[i] : 0.0f;
+            s += dzv;
+            q += dzv * yh;
+        }
+    }
+    sh[0][threadIdx.x] = s;
+    sh[1][threadIdx.x] = q;
+    __syncthreads();
+    // rows ro = 0..lanes-1 of channel c sit at threadIdx c + ro * C: fixed halving tree over ro
+    for (int n = lanes; n > 1;) {
+        const int half = (n + 1) / 2;
+        if (ro + half < n) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + half * C];
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + half * C];
+        }
+        n = half;
+        __syncthreads();
+    }
+    if (ro == 0) {
+        part[static_cast<int64_t>(blockIdx.x) * 2 * C + c] = sh[0][c];
+        part[static_cast<int64_t>(blockIdx.x) * 2 * C + C + c] = sh[1][c];
+    }
+}
+
+// dy = gamma * rstd / N * (N dz - sum dz - yhat * sum(dz yhat)) for the 8 voxels of every
+// window, as BF16 for the GEMMs.
+__global__ void bn_bwd_pool_apply_kernel(const float *__restrict__ dpool, const uint8_t *__restrict__ arg,
+                                         const float *__restrict__ y, const float *__restrict__ mean,
+                                         const float *__restrict__ rstd, const float *__restrict__ gamma,
+                                         const float *__restrict__ beta, const float *__restrict__ dgamma,
+                                         const float *__restrict__ dbeta, int64_t n_win, int64_t P, PoolGeom pg,
+                                         bf16 *__restrict__ dy) {
+    const int C = pg.C;
+    const float N = static_cast<float>(P);
+    const int64_t total = n_win * C;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < total;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t w = i / C;
+        const int c = static_cast<int>(i - w * C);
+        const int a = arg[i];
+        const float dp = dpool[i];
+        const float mu = mean[c], rs = rstd[c], ga = gamma[c], be = beta[c], db = dbeta[c], dg = dgamma[c];
+        const int64_t v0 = window_voxel(w, 0, pg);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int64_t pos = v0 + (static_cast<int64_t>((q >> 2)) * pg.H + ((q >> 1) & 1)) * pg.W + (q & 1);
+            const float yh = (y[pos * C + c] - mu) * rs;
+            const float dzv = (q == a && ga * yh + be > 0.0f) ? dp : 0.0f;
+            dy[pos * C + c] = __float2bfloat16_rn(ga * rs / N * (N * dzv - db - yh * dg));
+        }
+    }
+}
+
 // Inference: the running statistics take the place of the batch statistics.
 __global__ void bn_eval_kernel(const float *__restrict__ run_mean, const float *__restrict__ run_var, int C,
                                float eps, float *__restrict__ mean, float *__restrict__ rstd) {
@@ -165,55 +234,7 @@ __global__ void bn_relu_pool_kernel(const float *__restrict__ y, const float *__
     }
 }
 
-// Pool + ReLU backward: dz at the arg-max position (if its pre-activation is
-// positive) = incoming gradient; dz must be zero beforehand.
-__global__ void pool_relu_bwd_kernel(const float *__restrict__ dpool, const uint8_t *__restrict__ arg,
-                                     const float *__restrict__ y, const float *__restrict__ mean,
-                                     const float *__restrict__ rstd, const float *__restrict__ gamma,
-                                     const float *__restrict__ beta, int B, int D, int H, int W, int C,
-                                     float *__restrict__ dz) {
-    const int D2 = D / 2, H2 = H / 2, W2 = W / 2;
-    const int64_t total = static_cast<int64_t>(B) * D2 * H2 * W2 * C;
-    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < total;
-         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int c = static_cast<int>(i % C);
-        int64_t r = i / C;
-        const int x2 = static_cast<int>(r % W2);
-        const int y2 = static_cast<int>((r / W2) % H2);
-        const int z2 = static_cast<int>((r / (static_cast<int64_t>(W2) * H2)) % D2);
-        const int64_t b = r / (static_cast<int64_t>(W2) * H2 * D2);
-        const int q = arg[i];
-        const int dz_ = q >> 2, dy = (q >> 1) & 1, dx = q & 1;
-        const int64_t pos = ((b * D + 2 * z2 + dz_) * H + 2 * y2 + dy) * W + 2 * x2 + dx;
-        const float zpre = gamma[c] * ((y[pos * C + c] - mean[c]) * rstd[c]) + beta[c];
-        if (zpre > 0.0f) dz[pos * C + c] = dpool[i];
-    }
-}
 
-// Partial sums of dz and dz * yhat per channel.
-__global__ void bn_bwd_partial_kernel(const float *__restrict__ dz, const float *__restrict__ y,
-                                      const float *__restrict__ mean, const float *__restrict__ rstd, int64_t P,
-                                      int C, int rows_per_block, float *__restrict__ part) {
-    extern __shared__ float sh[];
-    for (int c = threadIdx.x; c < 2 * C; c += blockDim.x) sh[c] = 0.0f;
-    __syncthreads();
-    const int64_t r0 = static_cast<int64_t>(blockIdx.x) * rows_per_block;
-    const int64_t r1 = min(P, r0 + rows_per_block);
-    const int c = threadIdx.x % C, lanes = blockDim.x / C, ro = threadIdx.x / C;
-    float s = 0.0f, q = 0.0f;
-    if (ro < lanes) {
-        const float mu = mean[c], rs = rstd[c];
-        for (int64_t r = r0 + ro; r < r1; r += lanes) {
-            const float g = dz[r * C + c];
-            s += g;
-            q += g * ((y[r * C + c] - mu) * rs);
-        }
-        atomicAdd(&sh[c], s);
-        atomicAdd(&sh[C + c], q);
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < 2 * C; i += blockDim.x) part[static_cast<int64_t>(blockIdx.x) * 2 * C + i] = sh[i];
-}
 
 // dbeta = sum dz, dgamma = sum dz * yhat (written into the gradient vector).
 __global__ void __launch_bounds__(kFinThreads) bn_bwd_finish_kernel(const float *__restrict__ part, int nblk, int C,
@@ -227,21 +248,6 @@ __global__ void __launch_bounds__(kFinThreads) bn_bwd_finish_kernel(const float 
     dgamma[c] = static_cast<float>(q);
 }
 
-// dy = gamma * rstd / N * (N dz - sum dz - yhat * sum(dz yhat)), as BF16 for the GEMMs.
-__global__ void bn_bwd_apply_kernel(const float *__restrict__ dz, const float *__restrict__ y,
-                                    const float *__restrict__ mean, const float *__restrict__ rstd,
-                                    const float *__restrict__ gamma, const float *__restrict__ dgamma,
-                                    const float *__restrict__ dbeta, int64_t P, int C, bf16 *__restrict__ dy) {
-    const int64_t total = P * C;
-    const float N = static_cast<float>(P);
-    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < total;
-         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int c = static_cast<int>(i % C);
-        const float yh = (y[i] - mean[c]) * rstd[c];
-        const float v = gamma[c] * rstd[c] / N * (N * dz[i] - dbeta[c] - yh * dgamma[c]);
-        dy[i] = __float2bfloat16_rn(v);
-    }
-}
 
 // Head forward: features (BF16) -> FC1 -> ReLU -> dropout -> FC2 -> logit;
 // loss terms.  One block per sample.
@@ -470,7 +476,7 @@ struct nsfrb_clf_s {
     float *y[4] = {};
     float *mean[4] = {}, *rstd[4] = {};
     __nv_bfloat16 *dyb = nullptr;
-    float *dz = nullptr, *dact = nullptr, *part = nullptr;
+    float *dact = nullptr, *part = nullptr;
     float *feat = nullptr, *h1 = nullptr, *h1d = nullptr, *logit = nullptr, *loss_terms = nullptr, *loss = nullptr;
     float *dh1 = nullptr;
     float *labels_zero = nullptr;
@@ -496,20 +502,22 @@ nsfrb_status clf_fail(nsfrb_status st, const std::string &msg) {
     return st;
 }
 
-constexpr int kPartRows = 2048;
+constexpr int kWinPerBlock = 1024;   // pooling windows per block of the batch-norm backward partials
 
 // C[M][N] = A[M][K] B[N][K]^T; with gx.x set, A is the im2col matrix of gx (gathered).
+// With part set, also the column sums of C and of C^2 per 128-row tile: part[tile][2][N].
+constexpr int kGemmRows = 128;
 template <int G>
 nsfrb_status gemm_nt_g(int64_t M, int N, int K, const bf16 *A, const bf16 *B, float *C, gemm::Gather gx,
-                       cudaStream_t s) {
+                       cudaStream_t s, float *part = nullptr) {
     if (N <= 32) {
         const dim3 g2(static_cast<unsigned>((M + 127) / 128), static_cast<unsigned>((N + 31) / 32), 1);
         gemm::gemm_kernel<128, 32, false, G>
-            <<<g2, gemm::kThreads, 0, s>>>(static_cast<int>(M), N, K, A, K, B, K, C, N, 1, gx);
+            <<<g2, gemm::kThreads, 0, s>>>(static_cast<int>(M), N, K, A, K, B, K, C, N, 1, gx, part);
     } else {
         const dim3 grid(static_cast<unsigned>((M + 127) / 128), static_cast<unsigned>((N + 63) / 64), 1);
         gemm::gemm_kernel<128, 64, false, G>
-            <<<grid, gemm::kThreads, 0, s>>>(static_cast<int>(M), N, K, A, K, B, K, C, N, 1, gx);
+            <<<grid, gemm::kThreads, 0, s>>>(static_cast<int>(M), N, K, A, K, B, K, C, N, 1, gx, part);
     }
     return cudaGetLastError() == cudaSuccess ? NSFRB_OK : NSFRB_ECUDA;
 }
@@ -529,13 +537,13 @@ nsfrb_status gemm_tn_g(int M, int N, int64_t K, const bf16 *A, const bf16 *B, fl
     const dim3 grid(mt, nt, split);
     if (bm == 32)
         gemm::gemm_kernel<32, 128, true, G><<<grid, gemm::kThreads, 0, s>>>(M, N, static_cast<int>(K), A, M, B, N, C,
-                                                                             N, split, gx);
+                                                                             N, split, gx, nullptr);
     else if (bm == 64)
         gemm::gemm_kernel<64, 128, true, G><<<grid, gemm::kThreads, 0, s>>>(M, N, static_cast<int>(K), A, M, B, N, C,
-                                                                             N, split, gx);
+                                                                             N, split, gx, nullptr);
     else
         gemm::gemm_kernel<128, 64, true, G><<<grid, gemm::kThreads, 0, s>>>(M, N, static_cast<int>(K), A, M, B, N, C,
-                                                                             N, split, gx);
+                                                                             N, split, gx, nullptr);
     return cudaGetLastError() == cudaSuccess ? NSFRB_OK : NSFRB_ECUDA;
 }
 
@@ -554,11 +562,12 @@ nsfrb_status forward(nsfrb_clf_s *c, const bf16 *x, const float *labels, int B, 
     for (int l = 0; l < 4; ++l) {
         const int D = c->dims[l][0], H = c->dims[l][1], W = c->dims[l][2], Ci = c->dims[l][3], Co = cf.c[l];
         const int64_t P = static_cast<int64_t>(B) * D * H * W;
-        if (gemm_nt_g<1>(P, Co, 27 * Ci, nullptr, c->wb[l], c->y[l], gemm::make_gather(in, D, H, W, Ci), s) != NSFRB_OK)
+        // training: the GEMM also leaves the per-tile channel sums of y and y^2
+        if (gemm_nt_g<1>(P, Co, 27 * Ci, nullptr, c->wb[l], c->y[l], gemm::make_gather(in, D, H, W, Ci), s,
+                         train ? c->part : nullptr) != NSFRB_OK)
             return clf_cuda(c, cudaGetLastError(), "conv gemm");
         if (train) {
-            const int nblk = static_cast<int>((P + kPartRows - 1) / kPartRows);
-            bn_partial_kernel<<<nblk, kTB, 2 * Co * sizeof(float), s>>>(c->y[l], P, Co, kPartRows, c->part);
+            const int nblk = static_cast<int>((P + kGemmRows - 1) / kGemmRows);
             bn_finish_kernel<<<Co, kFinThreads, 0, s>>>(c->part, nblk, Co, P, 1e-5f, cf.bn_momentum, 1, c->mean[l],
                                                         c->rstd[l], c->run_mean + rs, c->run_var + rs);
         } else {
@@ -594,19 +603,25 @@ nsfrb_status backward(nsfrb_clf_s *c, const bf16 *x, const float *labels, int B,
     for (int l = 3; l >= 0; --l) {
         const int D = c->dims[l][0], H = c->dims[l][1], W = c->dims[l][2], Ci = c->dims[l][3], Co = cf.c[l];
         const int64_t P = static_cast<int64_t>(B) * D * H * W;
-        if (cudaMemsetAsync(c->dz, 0, sizeof(float) * P * Co, s) != cudaSuccess)
-            return clf_cuda(c, cudaGetLastError(), "memset");
-        pool_relu_bwd_kernel<<<grid_for(P / 8 * Co), kTB, 0, s>>>(c->dact, c->arg[l], c->y[l], c->mean[l], c->rstd[l],
-                                                                  c->params + c->off_g[l], c->params + c->off_b[l], B,
-                                                                  D, H, W, Co, c->dz);
-        const int nblk = static_cast<int>((P + kPartRows - 1) / kPartRows);
-        bn_bwd_partial_kernel<<<nblk, kTB, 2 * Co * sizeof(float), s>>>(c->dz, c->y[l], c->mean[l], c->rstd[l], P, Co,
-                                                                        kPartRows, c->part);
+        // max-pool, ReLU and batch-norm backward over the pooling windows (dz recomputed)
+        PoolGeom pg;
+        pg.D = D;
+        pg.H = H;
+        pg.W = W;
+        pg.C = Co;
+        pg.fW2 = gemm::make_fastdiv(W / 2);
+        pg.fH2 = gemm::make_fastdiv(H / 2);
+        pg.fD2 = gemm::make_fastdiv(D / 2);
+        const int64_t n_win = P / 8;
+        const int nblk = static_cast<int>((n_win + kWinPerBlock - 1) / kWinPerBlock);
+        bn_bwd_pool_partial_kernel<<<nblk, kTB, 0, s>>>(c->dact, c->arg[l], c->y[l], c->mean[l], c->rstd[l],
+                                                        c->params + c->off_g[l], c->params + c->off_b[l], n_win,
+                                                        kWinPerBlock, pg, c->part);
         bn_bwd_finish_kernel<<<Co, kFinThreads, 0, s>>>(c->part, nblk, Co, c->grads + c->off_g[l],
                                                         c->grads + c->off_b[l]);
-        bn_bwd_apply_kernel<<<grid_for(P * Co), kTB, 0, s>>>(c->dz, c->y[l], c->mean[l], c->rstd[l],
-                                                             c->params + c->off_g[l], c->grads + c->off_g[l],
-                                                             c->grads + c->off_b[l], P, Co, c->dyb);
+        bn_bwd_pool_apply_kernel<<<grid_for(n_win * Co), kTB, 0, s>>>(
+            c->dact, c->arg[l], c->y[l], c->mean[l], c->rstd[l], c->params + c->off_g[l], c->params + c->off_b[l],
+            c->grads + c->off_g[l], c->grads + c->off_b[l], n_win, P, pg, c->dyb);
         // weight gradient: dW[co][(k, ci)] = sum_p dy[p][co] col[p][(k, ci)], col gathered from the input
         const bf16 *in = (l == 0) ? x : c->act[l];
         if (gemm_tn_g<2>(Co, 27 * Ci, P, c->dyb, nullptr, c->grads + c->off_w[l], gemm::make_gather(in, D, H, W, Ci), s) !=
@@ -644,7 +659,7 @@ nsfrb_status nsfrb_clf_create(const nsfrb_clf_config *cfg, nsfrb_clf_t *out) {
         return clf_fail(NSFRB_EINVAL, "batch >= 1 and cutout sides multiples of 16 required");
     if (c.c0 < 8 || c.c0 % 8) return clf_fail(NSFRB_EINVAL, "c0 must be a positive multiple of 8");
     for (int l = 0; l < 4; ++l)
-        if (c.c[l] < 8 || c.c[l] % 8 || c.c[l] > 512) return clf_fail(NSFRB_EINVAL, "channels: multiples of 8 up to 512");
+        if (c.c[l] < 8 || c.c[l] % 8 || c.c[l] > kTB) return clf_fail(NSFRB_EINVAL, "channels: multiples of 8 up to 256");
     if (c.f < 1 || c.f > 1024) return clf_fail(NSFRB_EINVAL, "f must be 1..1024");
     if (!(c.dropout >= 0.0f && c.dropout < 1.0f)) return clf_fail(NSFRB_EINVAL, "dropout must be in [0, 1)");
     nsfrb_clf_s *m = new (std::nothrow) nsfrb_clf_s();
@@ -676,7 +691,8 @@ nsfrb_status nsfrb_clf_create(const nsfrb_clf_config *cfg, nsfrb_clf_t *out) {
         const int64_t P = static_cast<int64_t>(B) * m->dims[l][0] * m->dims[l][1] * m->dims[l][2];
         zmax = std::max(zmax, P * c.c[l]);
         dact = std::max(dact, P * m->dims[l][3]);
-        part = std::max(part, ((P + kPartRows - 1) / kPartRows) * 2 * c.c[l]);
+        part = std::max(part, ((P + kGemmRows - 1) / kGemmRows) * 2 * c.c[l]);
+        part = std::max(part, ((P / 8 + kWinPerBlock - 1) / kWinPerBlock) * 2 * c.c[l]);
     }
     int nc = 0;
     for (int l = 0; l < 4; ++l) nc += c.c[l];
@@ -702,7 +718,6 @@ nsfrb_status nsfrb_clf_create(const nsfrb_clf_config *cfg, nsfrb_clf_t *out) {
         A(reinterpret_cast<void **>(&m->rstd[l]), sizeof(float) * c.c[l]);
     }
     A(reinterpret_cast<void **>(&m->dyb), sizeof(bf16) * zmax);
-    A(reinterpret_cast<void **>(&m->dz), sizeof(float) * zmax);
     A(reinterpret_cast<void **>(&m->dact), sizeof(float) * dact);
     A(reinterpret_cast<void **>(&m->part), sizeof(float) * std::max<int64_t>(part, 2));
     A(reinterpret_cast<void **>(&m->feat), sizeof(float) * B * m->Fin);
@@ -916,7 +931,7 @@ void nsfrb_clf_destroy(nsfrb_clf_t clf) {
     if (!clf) return;
     cudaDeviceSynchronize();
     void *ptrs[] = {clf->params, clf->grads, clf->adam_m, clf->adam_v, clf->run_mean, clf->run_var,
-                    clf->dyb, clf->dz, clf->dact, clf->part, clf->feat, clf->h1, clf->h1d, clf->dh1, clf->logit,
+                    clf->dyb, clf->dact, clf->part, clf->feat, clf->h1, clf->h1d, clf->dh1, clf->logit,
                     clf->loss_terms, clf->loss};
     for (void *p : ptrs) cudaFree(p);
     for (int l = 0; l < 4; ++l) {

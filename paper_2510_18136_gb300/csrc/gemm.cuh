@@ -114,7 +114,7 @@ template <int BM, int BN, bool TRANS, int G = 0>
 __global__ void __launch_bounds__(kThreads) gemm_kernel(int M, int N, int K, const __nv_bfloat16 *__restrict__ A,
                                                         int64_t lda, const __nv_bfloat16 *__restrict__ B,
                                                         int64_t ldb, float *__restrict__ C, int64_t ldc,
-                                                        int k_split, Gather gx) {
+                                                        int k_split, Gather gx, float *__restrict__ part) {
     static_assert(G == 0 || (G == 1 && !TRANS) || (G == 2 && TRANS), "gather mode / layout mismatch");
     constexpr int WM = (BN >= 64) ? 2 : 4;    // warps along M
     constexpr int WN = 4 / WM;                // warps along N
@@ -297,6 +297,51 @@ __global__ void __launch_bounds__(kThreads) gemm_kernel(int M, int N, int K, con
 
     // epilogue: fragment (row = lane/4 [+8], col = 2*(lane%4) + {0,1})
     const int g = lane >> 2, tg = lane & 3;
+    if constexpr (!TRANS) {
+        if (part != nullptr) {
+            // column sums of this tile's rows (and of their squares), for batch-norm
+            // statistics: lanes, then the WM warps along M, in a fixed order;
+            // part[blockIdx.x][0][col] and part[blockIdx.x][1][col]
+            float (*red)[BN][2] = reinterpret_cast<float (*)[BN][2]>(&sm);
+#pragma unroll
+            for (int jn = 0; jn < NI; ++jn)
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    float cs = 0.0f, cq = 0.0f;
+#pragma unroll
+                    for (int i = 0; i < MI; ++i)
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const int row = m0 + wm * TM + i * 16 + g + 8 * h;
+                            const float v = row < M ? acc[i][jn][2 * h + e] : 0.0f;
+                            cs += v;
+                            cq += v * v;
+                        }
+#pragma unroll
+                    for (int o = 4; o < 32; o <<= 1) {
+                        cs += __shfl_xor_sync(0xffffffffu, cs, o);
+                        cq += __shfl_xor_sync(0xffffffffu, cq, o);
+                    }
+                    if (g == 0) {
+                        const int col = wn * TN + jn * 8 + 2 * tg + e;
+                        red[wm][col][0] = cs;
+                        red[wm][col][1] = cq;
+                    }
+                }
+            __syncthreads();
+            for (int col = tid; col < BN; col += kThreads) {
+                float cs = 0.0f, cq = 0.0f;
+                for (int w = 0; w < WM; ++w) {
+                    cs += red[w][col][0];
+                    cq += red[w][col][1];
+                }
+                if (n0 + col < N) {
+                    part[(static_cast<int64_t>(blockIdx.x) * 2) * N + n0 + col] = cs;
+                    part[(static_cast<int64_t>(blockIdx.x) * 2 + 1) * N + n0 + col] = cq;
+                }
+            }
+        }
+    }
 #pragma unroll
     for (int i = 0; i < MI; ++i)
 #pragma unroll
