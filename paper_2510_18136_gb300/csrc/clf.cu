@@ -502,7 +502,7 @@ nsfrb_status clf_fail(nsfrb_status st, const std::string &msg) {
     return st;
 }
 
-constexpr int kWinPerBlock = 1024;   // pooling windows per block of the batch-norm backward partials
+constexpr int kWinPerBlock = 64;     // pooling windows per block of the batch-norm backward partials
 
 // C[M][N] = A[M][K] B[N][K]^T; with gx.x set, A is the im2col matrix of gx (gathered).
 // With part set, also the column sums of C and of C^2 per 128-row tile: part[tile][2][N].
