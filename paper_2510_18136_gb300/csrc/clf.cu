@@ -21,6 +21,7 @@
 
 #include <cuda_bf16.h>
 
+#include "conv3.cuh"
 #include "gemm.cuh"
 #include "nsfrb_debug.h"
 #include "plan_internal.h"
@@ -482,6 +483,7 @@ struct nsfrb_clf_s {
     float *labels_zero = nullptr;
     int64_t zmax = 0, dact_elems = 0;
     int part_blocks = 0;
+    int max_smem = 0, n_sm = 0;   // device properties for the convolution kernels
     nsfrb_status latched = NSFRB_OK;
 };
 
@@ -547,6 +549,51 @@ nsfrb_status gemm_tn_g(int M, int N, int64_t K, const bf16 *A, const bf16 *B, fl
     return cudaGetLastError() == cudaSuccess ? NSFRB_OK : NSFRB_ECUDA;
 }
 
+// 3x3x3 convolution y = conv(x, w) by the halo-tile kernel when the channel pair has an
+// instance, the volume divides into 2 x 8 x 8 bricks and the shared memory fits (two halo
+// buffers if possible, else one).  Returns false when it does not apply (nothing launched).
+template <int CI, int CO, int NBUF>
+bool conv3_try(const bf16 *x, const bf16 *w, float *y, float *part, int B, int D, int H, int W, int max_smem,
+               int n_sm, cudaStream_t s, cudaError_t &err) {
+    const size_t smem = conv3::Shape<CI, CO>::smem(NBUF);
+    if (smem > static_cast<size_t>(max_smem)) return false;
+    static int blocks_per_sm = 0;   // per instance: attribute set and occupancy read once
+    if (blocks_per_sm == 0) {
+        err = cudaFuncSetAttribute(conv3::conv3_kernel<CI, CO, NBUF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   static_cast<int>(smem));
+        if (err == cudaSuccess)
+            err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, conv3::conv3_kernel<CI, CO, NBUF>,
+                                                                conv3::kThreads, smem);
+        if (err != cudaSuccess) return true;
+        blocks_per_sm = std::max(blocks_per_sm, 1);
+    }
+    const int n_bricks = B * (D / conv3::BZ) * (H / conv3::BY) * (W / conv3::BX);
+    const int grid = std::min(n_bricks, blocks_per_sm * n_sm);
+    conv3::conv3_kernel<CI, CO, NBUF><<<grid, conv3::kThreads, smem, s>>>(x, w, y, part, D, H, W, n_bricks);
+    err = cudaGetLastError();
+    return true;
+}
+
+template <int CI, int CO>
+bool conv3_pair(const bf16 *x, const bf16 *w, float *y, float *part, int B, int D, int H, int W, int max_smem,
+                int n_sm, cudaStream_t s, cudaError_t &err) {
+    return conv3_try<CI, CO, 2>(x, w, y, part, B, D, H, W, max_smem, n_sm, s, err) ||
+           conv3_try<CI, CO, 1>(x, w, y, part, B, D, H, W, max_smem, n_sm, s, err);
+}
+
+bool conv3_launch(int CI, int CO, const bf16 *x, const bf16 *w, float *y, float *part, int B, int D, int H, int W,
+                  int max_smem, int n_sm, cudaStream_t s, cudaError_t &err) {
+    err = cudaSuccess;
+    if (D % conv3::BZ || H % conv3::BY || W % conv3::BX) return false;
+#define NSFRB_CONV3(A, Bc)                                                                               \
+    if (CI == A && CO == Bc) return conv3_pair<A, Bc>(x, w, y, part, B, D, H, W, max_smem, n_sm, s, err);
+    NSFRB_CONV3(16, 16) NSFRB_CONV3(16, 32) NSFRB_CONV3(16, 64)
+    NSFRB_CONV3(32, 16) NSFRB_CONV3(32, 32) NSFRB_CONV3(32, 64)
+    NSFRB_CONV3(64, 16) NSFRB_CONV3(64, 32) NSFRB_CONV3(64, 64)
+#undef NSFRB_CONV3
+    return false;
+}
+
 nsfrb_status gemm_nt(int64_t M, int N, int K, const bf16 *A, const bf16 *B, float *C, cudaStream_t s) {
     return gemm_nt_g<0>(M, N, K, A, B, C, gemm::Gather{}, s);
 }
@@ -562,10 +609,15 @@ nsfrb_status forward(nsfrb_clf_s *c, const bf16 *x, const float *labels, int B, 
     for (int l = 0; l < 4; ++l) {
         const int D = c->dims[l][0], H = c->dims[l][1], W = c->dims[l][2], Ci = c->dims[l][3], Co = cf.c[l];
         const int64_t P = static_cast<int64_t>(B) * D * H * W;
-        // training: the GEMM also leaves the per-tile channel sums of y and y^2
-        if (gemm_nt_g<1>(P, Co, 27 * Ci, nullptr, c->wb[l], c->y[l], gemm::make_gather(in, D, H, W, Ci), s,
-                         train ? c->part : nullptr) != NSFRB_OK)
+        // training: the convolution also leaves the per-tile (128-row) channel sums of y and y^2
+        cudaError_t ce;
+        if (conv3_launch(Ci, Co, in, c->wb[l], c->y[l], train ? c->part : nullptr, B, D, H, W, c->max_smem, c->n_sm,
+                         s, ce)) {
+            if (ce != cudaSuccess) return clf_cuda(c, ce, "conv3");
+        } else if (gemm_nt_g<1>(P, Co, 27 * Ci, nullptr, c->wb[l], c->y[l], gemm::make_gather(in, D, H, W, Ci), s,
+                                train ? c->part : nullptr) != NSFRB_OK) {
             return clf_cuda(c, cudaGetLastError(), "conv gemm");
+        }
         if (train) {
             const int nblk = static_cast<int>((P + kGemmRows - 1) / kGemmRows);
             bn_finish_kernel<<<Co, kFinThreads, 0, s>>>(c->part, nblk, Co, P, 1e-5f, cf.bn_momentum, 1, c->mean[l],
@@ -629,9 +681,13 @@ nsfrb_status backward(nsfrb_clf_s *c, const bf16 *x, const float *labels, int B,
             return clf_cuda(c, cudaGetLastError(), "weight gemm");
         if (l > 0) {
             // input gradient: a convolution of dy with the flipped, transposed weights
-            if (gemm_nt_g<1>(P, Ci, 27 * Co, nullptr, c->wf[l], c->dact, gemm::make_gather(c->dyb, D, H, W, Co), s) !=
-                NSFRB_OK)
+            cudaError_t ce;
+            if (conv3_launch(Co, Ci, c->dyb, c->wf[l], c->dact, nullptr, B, D, H, W, c->max_smem, c->n_sm, s, ce)) {
+                if (ce != cudaSuccess) return clf_cuda(c, ce, "conv3 input gradient");
+            } else if (gemm_nt_g<1>(P, Ci, 27 * Co, nullptr, c->wf[l], c->dact, gemm::make_gather(c->dyb, D, H, W, Co),
+                                    s) != NSFRB_OK) {
                 return clf_cuda(c, cudaGetLastError(), "input gemm");
+            }
         }
     }
     return clf_cuda(c, cudaGetLastError(), "backward");
@@ -696,6 +752,12 @@ nsfrb_status nsfrb_clf_create(const nsfrb_clf_config *cfg, nsfrb_clf_t *out) {
     }
     int nc = 0;
     for (int l = 0; l < 4; ++l) nc += c.c[l];
+    {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&m->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cudaDeviceGetAttribute(&m->n_sm, cudaDevAttrMultiProcessorCount, dev);
+    }
     bool ok = true;
     auto A = [&](void **p, size_t bytes) {
         if (ok && cudaMalloc(p, bytes) != cudaSuccess) ok = false;
