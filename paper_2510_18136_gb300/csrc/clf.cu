@@ -308,9 +308,9 @@ __global__ void head_bwd_kernel(int B, int Fin, int F, const float *__restrict__
                                 const float *__restrict__ h1, const float *__restrict__ h1d,
                                 const float *__restrict__ logit, const float *__restrict__ labels,
                                 const float *__restrict__ w1, const float *__restrict__ w2, float p, uint2 key,
-                                uint32_t step, float *__restrict__ dh1, float *__restrict__ g_w1,
-                                float *__restrict__ g_b1, float *__restrict__ g_w2, float *__restrict__ g_b2) {
-    // dh1[b][f] and the FC2 gradients
+                                uint32_t step, float *__restrict__ dh1, float *__restrict__ g_b1,
+                                float *__restrict__ g_w2, float *__restrict__ g_b2) {
+    // dh1[b][f] and the FC2 gradients (the FC1 weight gradient: head_dw1_kernel)
     for (int i = threadIdx.x; i < B * F; i += blockDim.x) {
         const int b = i / F, f = i % F;
         const float dz = (1.0f / (1.0f + expf(-logit[b])) - labels[b]) / static_cast<float>(B);
@@ -339,8 +339,15 @@ __global__ void head_bwd_kernel(int B, int Fin, int F, const float *__restrict__
         for (int b = 0; b < B; ++b) s += (1.0f / (1.0f + expf(-logit[b])) - labels[b]) / static_cast<float>(B);
         g_b2[0] = s;
     }
-    for (int i = threadIdx.x; i < F * Fin; i += blockDim.x) {
-        const int f = i / Fin, k = i % Fin;
+}
+
+// FC1 weight gradient g_w1[f][k] = sum_b dh1[b][f] feat[b][k] (b ascending), one output per thread.
+__global__ void head_dw1_kernel(int B, int Fin, int F, const float *__restrict__ feat, const float *__restrict__ dh1,
+                                float *__restrict__ g_w1) {
+    const int64_t n = static_cast<int64_t>(F) * Fin;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int f = static_cast<int>(i / Fin), k = static_cast<int>(i - static_cast<int64_t>(f) * Fin);
         float s = 0.0f;
         for (int b = 0; b < B; ++b) s += dh1[b * F + f] * feat[static_cast<int64_t>(b) * Fin + k];
         g_w1[i] = s;
@@ -484,6 +491,8 @@ struct nsfrb_clf_s {
     int64_t zmax = 0, dact_elems = 0;
     int part_blocks = 0;
     int max_smem = 0, n_sm = 0;   // device properties for the convolution kernels
+    float *wpart = nullptr;       // per-CTA weight-gradient partials
+    int64_t wpart_elems = 0;
     nsfrb_status latched = NSFRB_OK;
 };
 
@@ -581,6 +590,44 @@ bool conv3_pair(const bf16 *x, const bf16 *w, float *y, float *part, int B, int 
            conv3_try<CI, CO, 1>(x, w, y, part, B, D, H, W, max_smem, n_sm, s, err);
 }
 
+// Weight gradient dW = sum_voxels dy x(tap) by the halo-tile kernel (into the partial workspace,
+// then a fixed-order sum into dw) when the channel pair keeps <= 128 accumulators per lane, the
+// volume divides into bricks and the shared memory fits; false when it does not apply.
+template <int CI, int CO>
+bool wgrad_pair(const bf16 *x, const bf16 *dy, float *wpart, int64_t wpart_elems, float *dw, int B, int D, int H,
+                int W, int max_smem, int n_sm, cudaStream_t s, cudaError_t &err) {
+    using S = conv3::WgShape<CI, CO>;
+    if (S::ACC > 128 || S::smem > static_cast<size_t>(max_smem)) return false;
+    const int n_bricks = B * (D / conv3::BZ) * (H / conv3::BY) * (W / conv3::BX);
+    const int grid = std::min(n_bricks, n_sm);
+    const int64_t n = static_cast<int64_t>(CO) * 27 * CI;
+    if (static_cast<int64_t>(grid) * n > wpart_elems) return false;
+    static bool attr = false;
+    if (!attr) {
+        err = cudaFuncSetAttribute(conv3::conv3_wgrad_kernel<CI, CO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   static_cast<int>(S::smem));
+        if (err != cudaSuccess) return true;
+        attr = true;
+    }
+    conv3::conv3_wgrad_kernel<CI, CO><<<grid, conv3::kWgThreads, S::smem, s>>>(x, dy, wpart, D, H, W, n_bricks);
+    conv3::wgrad_reduce_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(wpart, grid, n, dw);
+    err = cudaGetLastError();
+    return true;
+}
+
+bool wgrad_launch(int CI, int CO, const bf16 *x, const bf16 *dy, float *wpart, int64_t wpart_elems, float *dw, int B,
+                  int D, int H, int W, int max_smem, int n_sm, cudaStream_t s, cudaError_t &err) {
+    err = cudaSuccess;
+    if (D % conv3::BZ || H % conv3::BY || W % conv3::BX) return false;
+#define NSFRB_WGRAD(A, Bc)                                                                                 \
+    if (CI == A && CO == Bc)                                                                               \
+        return wgrad_pair<A, Bc>(x, dy, wpart, wpart_elems, dw, B, D, H, W, max_smem, n_sm, s, err);
+    NSFRB_WGRAD(16, 16) NSFRB_WGRAD(16, 32) NSFRB_WGRAD(16, 64)
+    NSFRB_WGRAD(32, 16) NSFRB_WGRAD(32, 32) NSFRB_WGRAD(64, 16)
+#undef NSFRB_WGRAD
+    return false;
+}
+
 bool conv3_launch(int CI, int CO, const bf16 *x, const bf16 *w, float *y, float *part, int B, int D, int H, int W,
                   int max_smem, int n_sm, cudaStream_t s, cudaError_t &err) {
     err = cudaSuccess;
@@ -648,8 +695,10 @@ nsfrb_status backward(nsfrb_clf_s *c, const bf16 *x, const float *labels, int B,
     const uint2 key = make_uint2(static_cast<uint32_t>(cf.seed), static_cast<uint32_t>(cf.seed >> 32));
     head_bwd_kernel<<<1, kTB, 0, s>>>(B, c->Fin, cf.f, c->feat, c->h1, c->h1d, c->logit, labels,
                                       c->params + c->off_f1w, c->params + c->off_f2w, cf.dropout, key,
-                                      static_cast<uint32_t>(c->step), c->dh1, c->grads + c->off_f1w,
-                                      c->grads + c->off_f1b, c->grads + c->off_f2w, c->grads + c->off_f2b);
+                                      static_cast<uint32_t>(c->step), c->dh1, c->grads + c->off_f1b,
+                                      c->grads + c->off_f2w, c->grads + c->off_f2b);
+    head_dw1_kernel<<<grid_for(static_cast<int64_t>(cf.f) * c->Fin), kTB, 0, s>>>(B, c->Fin, cf.f, c->feat, c->dh1,
+                                                                                c->grads + c->off_f1w);
     head_dfeat_kernel<<<grid_for(static_cast<int64_t>(B) * c->Fin), kTB, 0, s>>>(B, c->Fin, cf.f, c->dh1,
                                                                                c->params + c->off_f1w, c->dact);
     for (int l = 3; l >= 0; --l) {
@@ -676,9 +725,14 @@ nsfrb_status backward(nsfrb_clf_s *c, const bf16 *x, const float *labels, int B,
             c->grads + c->off_g[l], c->grads + c->off_b[l], n_win, P, pg, c->dyb);
         // weight gradient: dW[co][(k, ci)] = sum_p dy[p][co] col[p][(k, ci)], col gathered from the input
         const bf16 *in = (l == 0) ? x : c->act[l];
-        if (gemm_tn_g<2>(Co, 27 * Ci, P, c->dyb, nullptr, c->grads + c->off_w[l], gemm::make_gather(in, D, H, W, Ci), s) !=
-            NSFRB_OK)
+        cudaError_t we;
+        if (wgrad_launch(Ci, Co, in, c->dyb, c->wpart, c->wpart_elems, c->grads + c->off_w[l], B, D, H, W,
+                         c->max_smem, c->n_sm, s, we)) {
+            if (we != cudaSuccess) return clf_cuda(c, we, "conv3 weight gradient");
+        } else if (gemm_tn_g<2>(Co, 27 * Ci, P, c->dyb, nullptr, c->grads + c->off_w[l],
+                                gemm::make_gather(in, D, H, W, Ci), s) != NSFRB_OK) {
             return clf_cuda(c, cudaGetLastError(), "weight gemm");
+        }
         if (l > 0) {
             // input gradient: a convolution of dy with the flipped, transposed weights
             cudaError_t ce;
@@ -780,6 +834,10 @@ nsfrb_status nsfrb_clf_create(const nsfrb_clf_config *cfg, nsfrb_clf_t *out) {
         A(reinterpret_cast<void **>(&m->rstd[l]), sizeof(float) * c.c[l]);
     }
     A(reinterpret_cast<void **>(&m->dyb), sizeof(bf16) * zmax);
+    for (int l = 0; l < 4; ++l)
+        m->wpart_elems = std::max<int64_t>(m->wpart_elems, static_cast<int64_t>(std::max(m->n_sm, 1)) * c.c[l] * 27 *
+                                                               m->dims[l][3]);
+    A(reinterpret_cast<void **>(&m->wpart), sizeof(float) * m->wpart_elems);
     A(reinterpret_cast<void **>(&m->dact), sizeof(float) * dact);
     A(reinterpret_cast<void **>(&m->part), sizeof(float) * std::max<int64_t>(part, 2));
     A(reinterpret_cast<void **>(&m->feat), sizeof(float) * B * m->Fin);
@@ -993,7 +1051,7 @@ void nsfrb_clf_destroy(nsfrb_clf_t clf) {
     if (!clf) return;
     cudaDeviceSynchronize();
     void *ptrs[] = {clf->params, clf->grads, clf->adam_m, clf->adam_v, clf->run_mean, clf->run_var,
-                    clf->dyb, clf->dact, clf->part, clf->feat, clf->h1, clf->h1d, clf->dh1, clf->logit,
+                    clf->dyb, clf->wpart, clf->dact, clf->part, clf->feat, clf->h1, clf->h1d, clf->dh1, clf->logit,
                     clf->loss_terms, clf->loss};
     for (void *p : ptrs) cudaFree(p);
     for (int l = 0; l < 4; ++l) {

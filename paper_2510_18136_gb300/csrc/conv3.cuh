@@ -193,3 +193,168 @@ __global__ void __launch_bounds__(kThreads) conv3_kernel(const bf16 *__restrict_
 
 }  // namespace conv3
 }  // namespace nsfrb
+
+namespace nsfrb {
+namespace conv3 {
+
+// Weight gradient of the same convolution: dW[co][tap][ci] = sum_voxels dy[v][co] x[v + tap][ci].
+// A CTA takes a contiguous range of bricks; per brick the input halo and the brick's 128 x CO
+// tile of dy are staged in shared memory (double buffered) and 8 warps each accumulate up to 4
+// taps (warp w: taps w, w + 8, w + 16, w + 24) in registers: A = dy^T (ldmatrix.trans of the dy
+// tile), B = the halo shifted by the tap (ldmatrix.trans with one row address per lane).  The
+// CTA writes its sums to partial[blockIdx.x][CO][27 CI]; wgrad_reduce_kernel adds the CTAs'
+// partials in order.
+constexpr int kWgThreads = 256;
+
+template <int CI, int CO>
+struct WgShape {
+    static constexpr int HP = CI + 8, YP = CO + 8;
+    static constexpr size_t h_bytes = sizeof(bf16) * HV * HP;
+    static constexpr size_t y_bytes = sizeof(bf16) * BZ * BY * BX * YP;
+    static constexpr size_t smem = 2 * (h_bytes + y_bytes);
+    static constexpr int ACC = 4 * (CO / 16) * (CI / 8) * 4;   // accumulator floats per lane
+};
+
+template <int CI, int CO>
+__global__ void __launch_bounds__(kWgThreads, 1) conv3_wgrad_kernel(const bf16 *__restrict__ x,
+                                                                    const bf16 *__restrict__ dy,
+                                                                    float *__restrict__ partial, int D, int H, int W,
+                                                                    int n_bricks) {
+    using S = WgShape<CI, CO>;
+    constexpr int MI = CO / 16, NI = CI / 8;
+    static_assert(CI % 16 == 0 && CO % 16 == 0, "channels must be multiples of 16");
+    extern __shared__ __align__(128) unsigned char smem[];
+    bf16 *s_h = reinterpret_cast<bf16 *>(smem);                      // [2][HV][HP]
+    bf16 *s_y = reinterpret_cast<bf16 *>(smem + 2 * S::h_bytes);     // [2][128][YP]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nxb = W / BX, nyb = H / BY, nzb = D / BZ;
+    const int bi0 = static_cast<int>(static_cast<int64_t>(blockIdx.x) * n_bricks / gridDim.x);
+    const int bi1 = static_cast<int>(static_cast<int64_t>(blockIdx.x + 1) * n_bricks / gridDim.x);
+
+    auto brick_origin = [&](int bi, int &b, int &z0, int &y0, int &x0) {
+        const int xb = bi % nxb, t1 = bi / nxb, yb = t1 % nyb, t2 = t1 / nyb, zb = t2 % nzb;
+        b = t2 / nzb;
+        z0 = zb * BZ;
+        y0 = yb * BY;
+        x0 = xb * BX;
+    };
+    auto load = [&](int bi, int nb) {
+        int b, z0, y0, x0;
+        brick_origin(bi, b, z0, y0, x0);
+        bf16 *hd = s_h + static_cast<size_t>(nb) * HV * S::HP;
+        for (int c = tid; c < HV * (CI / 8); c += kWgThreads) {
+            const int hv = c / (CI / 8), cc = (c - hv * (CI / 8)) * 8;
+            const int hz = hv / (HY * HX), hy = (hv / HX) % HY, hx = hv % HX;
+            const int zz = z0 + hz - 1, yy = y0 + hy - 1, xx = x0 + hx - 1;
+            const bool ok = zz >= 0 && zz < D && yy >= 0 && yy < H && xx >= 0 && xx < W;
+            const bf16 *src = ok ? x + ((((static_cast<int64_t>(b) * D + zz) * H + yy) * W + xx) * CI + cc) : x;
+            gemm::cp_async16(hd + hv * S::HP + cc, src, ok);
+        }
+        bf16 *yd = s_y + static_cast<size_t>(nb) * 128 * S::YP;
+        for (int c = tid; c < 128 * (CO / 8); c += kWgThreads) {
+            const int r = c / (CO / 8), cc = (c - r * (CO / 8)) * 8;
+            const int64_t p = ((static_cast<int64_t>(b) * D + z0 + (r >> 6)) * H + y0 + ((r >> 3) & 7)) * W + x0 +
+                              (r & 7);
+            gemm::cp_async16(yd + r * S::YP + cc, dy + p * CO + cc, true);
+        }
+        gemm::cp_async_commit();
+    };
+
+    // the ldmatrix.trans row of this lane for B at step s: brick voxel 16 s + (lane & 7) +
+    // 8 ((lane >> 3) & 1), as a halo voxel of the centre tap (A rows: 16 s + (lane & 7) + 8 (lane >> 4))
+    const int jb = lane >> 3, rb = lane & 7;
+    int hr[8];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+        const int r = 16 * s + rb + 8 * (jb & 1);
+        hr[s] = (((r >> 6) + 1) * HY + ((r >> 3) & 7) + 1) * HX + (r & 7) + 1;
+    }
+    int toff[4];
+    bool tok[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int tap = warp + 8 * q;
+        tok[q] = tap < 27;
+        const int t = tok[q] ? tap : 0;
+        toff[q] = ((t / 9 - 1) * HY + (t / 3) % 3 - 1) * HX + t % 3 - 1;
+    }
+    float acc[4][MI][NI][4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int i = 0; i < MI; ++i)
+#pragma unroll
+            for (int j = 0; j < NI; ++j)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc[q][i][j][e] = 0.0f;
+
+    if (bi0 < bi1) load(bi0, 0);
+    int it = 0;
+    for (int bi = bi0; bi < bi1; ++bi, ++it) {
+        const int nb = it & 1;
+        if (bi + 1 < bi1) {
+            load(bi + 1, nb ^ 1);
+            gemm::cp_async_wait<1>();
+        } else {
+            gemm::cp_async_wait<0>();
+        }
+        __syncthreads();
+        const bf16 *hb = s_h + static_cast<size_t>(nb) * HV * S::HP;
+        const bf16 *yb = s_y + static_cast<size_t>(nb) * 128 * S::YP;
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            const int kk = 16 * s;
+            uint32_t af[MI][4];
+#pragma unroll
+            for (int i = 0; i < MI; ++i)
+                gemm::ldsm_x4_t(af[i][0], af[i][1], af[i][2], af[i][3],
+                                yb + (kk + rb + 8 * (jb >> 1)) * S::YP + 16 * i + 8 * (jb & 1));
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (!tok[q]) continue;
+                uint32_t bfr[NI][2];
+#pragma unroll
+                for (int jn = 0; jn < NI; jn += 2)
+                    gemm::ldsm_x4_t(bfr[jn][0], bfr[jn][1], bfr[jn + 1][0], bfr[jn + 1][1],
+                                    hb + (hr[s] + toff[q]) * S::HP + jn * 8 + 8 * (jb >> 1));
+#pragma unroll
+                for (int i = 0; i < MI; ++i)
+#pragma unroll
+                    for (int jn = 0; jn < NI; ++jn) gemm::mma_bf16(acc[q][i][jn], af[i], bfr[jn][0], bfr[jn][1]);
+            }
+        }
+        __syncthreads();
+    }
+
+    // partial[blockIdx.x][co][tap * CI + ci]
+    const int g = lane >> 2, tg = lane & 3;
+    float *out = partial + static_cast<int64_t>(blockIdx.x) * CO * 27 * CI;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (!tok[q]) continue;
+        const int tap = warp + 8 * q;
+#pragma unroll
+        for (int i = 0; i < MI; ++i)
+#pragma unroll
+            for (int jn = 0; jn < NI; ++jn)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int co = 16 * i + g + 8 * h;
+                    *reinterpret_cast<float2 *>(out + static_cast<int64_t>(co) * 27 * CI + tap * CI + jn * 8 + 2 * tg) =
+                        make_float2(acc[q][i][jn][2 * h], acc[q][i][jn][2 * h + 1]);
+                }
+    }
+}
+
+// out[i] = sum over c = 0..n_part-1 of partial[c][i], in that order.
+__global__ void wgrad_reduce_kernel(const float *__restrict__ partial, int n_part, int64_t n, float *__restrict__ out) {
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        float s = 0.0f;
+        for (int c = 0; c < n_part; ++c) s += partial[static_cast<int64_t>(c) * n + i];
+        out[i] = s;
+    }
+}
+
+}  // namespace conv3
+}  // namespace nsfrb
