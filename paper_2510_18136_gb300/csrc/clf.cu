@@ -583,11 +583,32 @@ bool conv3_try(const bf16 *x, const bf16 *w, float *y, float *part, int B, int D
     return true;
 }
 
+// Resident CTAs per SM of an instance (0 if its shared memory does not fit).
+template <int CI, int CO, int NBUF>
+int conv3_occupancy(int max_smem) {
+    static int occ = -1;
+    if (occ < 0) {
+        const size_t smem = conv3::Shape<CI, CO>::smem(NBUF);
+        occ = 0;
+        if (smem <= static_cast<size_t>(max_smem) &&
+            cudaFuncSetAttribute(conv3::conv3_kernel<CI, CO, NBUF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(smem)) == cudaSuccess &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, conv3::conv3_kernel<CI, CO, NBUF>, conv3::kThreads,
+                                                          smem) != cudaSuccess)
+            occ = 0;
+        cudaGetLastError();
+    }
+    return occ;
+}
+
+// Two halo buffers unless one buffer keeps more CTAs (warps) resident per SM.
 template <int CI, int CO>
 bool conv3_pair(const bf16 *x, const bf16 *w, float *y, float *part, int B, int D, int H, int W, int max_smem,
                 int n_sm, cudaStream_t s, cudaError_t &err) {
-    return conv3_try<CI, CO, 2>(x, w, y, part, B, D, H, W, max_smem, n_sm, s, err) ||
-           conv3_try<CI, CO, 1>(x, w, y, part, B, D, H, W, max_smem, n_sm, s, err);
+    const int o2 = conv3_occupancy<CI, CO, 2>(max_smem), o1 = conv3_occupancy<CI, CO, 1>(max_smem);
+    if (o2 > 0 && o2 >= o1) return conv3_try<CI, CO, 2>(x, w, y, part, B, D, H, W, max_smem, n_sm, s, err);
+    if (o1 > 0) return conv3_try<CI, CO, 1>(x, w, y, part, B, D, H, W, max_smem, n_sm, s, err);
+    return false;
 }
 
 // Weight gradient dW = sum_voxels dy x(tap) by the halo-tile kernel (into the partial workspace,
