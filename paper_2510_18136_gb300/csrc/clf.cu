@@ -104,8 +104,21 @@ __global__ void __launch_bounds__(kFinThreads) bn_finish_kernel(const float *__r
 // Window w of the pooled volume [B][D/2][H/2][W/2] and its voxel q (dz, dy, dx bits).
 struct PoolGeom {
     int D, H, W, C;
-    gemm::FastDiv fW2, fH2, fD2;
+    gemm::FastDiv fW2, fH2, fD2, fC;
 };
+
+inline PoolGeom make_pool_geom(int D, int H, int W, int C) {
+    PoolGeom pg;
+    pg.D = D;
+    pg.H = H;
+    pg.W = W;
+    pg.C = C;
+    pg.fW2 = gemm::make_fastdiv(W / 2);
+    pg.fH2 = gemm::make_fastdiv(H / 2);
+    pg.fD2 = gemm::make_fastdiv(D / 2);
+    pg.fC = gemm::make_fastdiv(C);
+    return pg;
+}
 
 __device__ __forceinline__ int64_t window_voxel(int64_t w, int q, const PoolGeom &g) {
     const int W2 = g.W / 2, H2 = g.H / 2, D2 = g.D / 2;
@@ -175,8 +188,8 @@ __global__ void bn_bwd_pool_apply_kernel(const float *__restrict__ dpool, const 
     const int64_t total = n_win * C;
     for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < total;
          i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int64_t w = i / C;
-        const int c = static_cast<int>(i - w * C);
+        const int w = gemm::fdiv(static_cast<int>(i), pg.fC);   // n_win * C < 2^31 (checked at creation)
+        const int c = static_cast<int>(i) - w * C;
         const int a = arg[i];
         const float dp = dpool[i];
         const float mu = mean[c], rs = rstd[c], ga = gamma[c], be = beta[c], db = dbeta[c], dg = dgamma[c];
@@ -204,25 +217,21 @@ __global__ void bn_eval_kernel(const float *__restrict__ run_mean, const float *
 // arg-max (first in (dz, dy, dx) order) for the backward pass.
 __global__ void bn_relu_pool_kernel(const float *__restrict__ y, const float *__restrict__ mean,
                                     const float *__restrict__ rstd, const float *__restrict__ gamma,
-                                    const float *__restrict__ beta, int B, int D, int H, int W, int C,
+                                    const float *__restrict__ beta, int64_t n_win, PoolGeom pg,
                                     bf16 *__restrict__ out, uint8_t *__restrict__ arg) {
-    const int D2 = D / 2, H2 = H / 2, W2 = W / 2;
-    const int64_t total = static_cast<int64_t>(B) * D2 * H2 * W2 * C;
+    const int C = pg.C;
+    const int64_t total = n_win * C;   // < 2^31 (checked at creation)
     for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < total;
          i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int c = static_cast<int>(i % C);
-        int64_t r = i / C;
-        const int x2 = static_cast<int>(r % W2);
-        const int y2 = static_cast<int>((r / W2) % H2);
-        const int z2 = static_cast<int>((r / (static_cast<int64_t>(W2) * H2)) % D2);
-        const int64_t b = r / (static_cast<int64_t>(W2) * H2 * D2);
+        const int w = gemm::fdiv(static_cast<int>(i), pg.fC);
+        const int c = static_cast<int>(i) - w * C;
         const float g = gamma[c], be = beta[c], mu = mean[c], rs = rstd[c];
+        const int64_t v0 = window_voxel(w, 0, pg);
         float m = -INFINITY;
         int a = 0;
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-            const int dz = q >> 2, dy = (q >> 1) & 1, dx = q & 1;
-            const int64_t pos = ((b * D + 2 * z2 + dz) * H + 2 * y2 + dy) * W + 2 * x2 + dx;
+            const int64_t pos = v0 + (static_cast<int64_t>(q >> 2) * pg.H + ((q >> 1) & 1)) * pg.W + (q & 1);
             float v = g * ((y[pos * C + c] - mu) * rs) + be;
             v = fmaxf(v, 0.0f);
             if (v > m) {
@@ -696,8 +705,8 @@ nsfrb_status forward(nsfrb_clf_s *c, const bf16 *x, const float *labels, int B, 
         }
         const int64_t npool = P / 8 * Co;
         bn_relu_pool_kernel<<<grid_for(npool), kTB, 0, s>>>(c->y[l], c->mean[l], c->rstd[l], c->params + c->off_g[l],
-                                                            c->params + c->off_b[l], B, D, H, W, Co, c->act[l + 1],
-                                                            c->arg[l]);
+                                                            c->params + c->off_b[l], P / 8, make_pool_geom(D, H, W, Co),
+                                                            c->act[l + 1], c->arg[l]);
         in = c->act[l + 1];
         rs += Co;
     }
@@ -726,14 +735,7 @@ nsfrb_status backward(nsfrb_clf_s *c, const bf16 *x, const float *labels, int B,
         const int D = c->dims[l][0], H = c->dims[l][1], W = c->dims[l][2], Ci = c->dims[l][3], Co = cf.c[l];
         const int64_t P = static_cast<int64_t>(B) * D * H * W;
         // max-pool, ReLU and batch-norm backward over the pooling windows (dz recomputed)
-        PoolGeom pg;
-        pg.D = D;
-        pg.H = H;
-        pg.W = W;
-        pg.C = Co;
-        pg.fW2 = gemm::make_fastdiv(W / 2);
-        pg.fH2 = gemm::make_fastdiv(H / 2);
-        pg.fD2 = gemm::make_fastdiv(D / 2);
+        const PoolGeom pg = make_pool_geom(D, H, W, Co);
         const int64_t n_win = P / 8;
         const int nblk = static_cast<int>((n_win + kWinPerBlock - 1) / kWinPerBlock);
         bn_bwd_pool_partial_kernel<<<nblk, kTB, 0, s>>>(c->dact, c->arg[l], c->y[l], c->mean[l], c->rstd[l],
@@ -789,8 +791,11 @@ nsfrb_status nsfrb_clf_create(const nsfrb_clf_config *cfg, nsfrb_clf_t *out) {
     if (c.batch < 1 || c.d < 16 || c.h < 16 || c.w < 16 || c.d % 16 || c.h % 16 || c.w % 16)
         return clf_fail(NSFRB_EINVAL, "batch >= 1 and cutout sides multiples of 16 required");
     if (c.c0 < 8 || c.c0 % 8) return clf_fail(NSFRB_EINVAL, "c0 must be a positive multiple of 8");
-    for (int l = 0; l < 4; ++l)
+    for (int l = 0; l < 4; ++l) {
         if (c.c[l] < 8 || c.c[l] % 8 || c.c[l] > kTB) return clf_fail(NSFRB_EINVAL, "channels: multiples of 8 up to 256");
+        if (static_cast<int64_t>(c.batch) * c.d * c.h * c.w * std::max(c.c[l], c.c0) >= (int64_t(1) << 31))
+            return clf_fail(NSFRB_EINVAL, "batch x cutout voxels x channels must stay below 2^31");
+    }
     if (c.f < 1 || c.f > 1024) return clf_fail(NSFRB_EINVAL, "f must be 1..1024");
     if (!(c.dropout >= 0.0f && c.dropout < 1.0f)) return clf_fail(NSFRB_EINVAL, "dropout must be in [0, 1)");
     nsfrb_clf_s *m = new (std::nothrow) nsfrb_clf_s();
