@@ -544,26 +544,41 @@ nsfrb_status gemm_nt_g(int64_t M, int N, int K, const bf16 *A, const bf16 *B, fl
 
 // C[M][N] (zeroed here) = A[K][M]^T B[K][N] with split-K over K; with gx.x set, B is the
 // im2col matrix of gx (gathered).
+// Tiles and split-K count of the TN GEMM: tile rows follow M (the output channels: 32 or 64 in
+// the network), wide tiles along N, about 4 CTAs per SM of 152.
+inline int tn_split(int M, int N, int64_t K, int &bm, int &mt, int &nt) {
+    bm = M <= 32 ? 32 : (M <= 64 ? 64 : 128);
+    const int bn = bm == 128 ? 64 : 128;
+    mt = (M + bm - 1) / bm;
+    nt = (N + bn - 1) / bn;
+    const int64_t k_steps = (K + gemm::BK - 1) / gemm::BK;
+    return std::max(1, static_cast<int>(std::min<int64_t>(k_steps, std::max<int64_t>(1, 4 * 152 / (mt * nt)))));
+}
+
+// With a workspace of wpart_elems floats that holds split x M x N, the splits' partials are summed in
+// split order (reproducible); otherwise they are added atomically.
 template <int G>
 nsfrb_status gemm_tn_g(int M, int N, int64_t K, const bf16 *A, const bf16 *B, float *C, gemm::Gather gx,
-                       cudaStream_t s) {
-    if (cudaMemsetAsync(C, 0, sizeof(float) * static_cast<size_t>(M) * N, s) != cudaSuccess) return NSFRB_ECUDA;
-    // tile rows follow M (the output channels: 32 or 64 in the network), wide tiles along N
-    const int bm = M <= 32 ? 32 : (M <= 64 ? 64 : 128), bn = bm == 128 ? 64 : 128;
-    const int mt = (M + bm - 1) / bm, nt = (N + bn - 1) / bn;
-    const int64_t k_steps = (K + gemm::BK - 1) / gemm::BK;
-    int split = static_cast<int>(std::min<int64_t>(k_steps, std::max<int64_t>(1, 4 * 152 / (mt * nt))));
-    split = std::max(split, 1);
+                       cudaStream_t s, float *wpart = nullptr, int64_t wpart_elems = 0) {
+    int bm, mt, nt;
+    const int split = tn_split(M, N, K, bm, mt, nt);
     const dim3 grid(mt, nt, split);
+    float *part = (wpart && static_cast<int64_t>(split) * M * N <= wpart_elems) ? wpart : nullptr;
+    if (!part && cudaMemsetAsync(C, 0, sizeof(float) * static_cast<size_t>(M) * N, s) != cudaSuccess)
+        return NSFRB_ECUDA;
     if (bm == 32)
         gemm::gemm_kernel<32, 128, true, G><<<grid, gemm::kThreads, 0, s>>>(M, N, static_cast<int>(K), A, M, B, N, C,
-                                                                             N, split, gx, nullptr);
+                                                                             N, split, gx, part);
     else if (bm == 64)
         gemm::gemm_kernel<64, 128, true, G><<<grid, gemm::kThreads, 0, s>>>(M, N, static_cast<int>(K), A, M, B, N, C,
-                                                                             N, split, gx, nullptr);
+                                                                             N, split, gx, part);
     else
         gemm::gemm_kernel<128, 64, true, G><<<grid, gemm::kThreads, 0, s>>>(M, N, static_cast<int>(K), A, M, B, N, C,
-                                                                             N, split, gx, nullptr);
+                                                                             N, split, gx, part);
+    if (part) {
+        const int64_t n = static_cast<int64_t>(M) * N;
+        conv3::wgrad_reduce_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(part, split, n, C);
+    }
     return cudaGetLastError() == cudaSuccess ? NSFRB_OK : NSFRB_ECUDA;
 }
 
@@ -753,7 +768,7 @@ nsfrb_status backward(nsfrb_clf_s *c, const bf16 *x, const float *labels, int B,
                          c->max_smem, c->n_sm, s, we)) {
             if (we != cudaSuccess) return clf_cuda(c, we, "conv3 weight gradient");
         } else if (gemm_tn_g<2>(Co, 27 * Ci, P, c->dyb, nullptr, c->grads + c->off_w[l],
-                                gemm::make_gather(in, D, H, W, Ci), s) != NSFRB_OK) {
+                                gemm::make_gather(in, D, H, W, Ci), s, c->wpart, c->wpart_elems) != NSFRB_OK) {
             return clf_cuda(c, cudaGetLastError(), "weight gemm");
         }
         if (l > 0) {
@@ -860,9 +875,15 @@ nsfrb_status nsfrb_clf_create(const nsfrb_clf_config *cfg, nsfrb_clf_t *out) {
         A(reinterpret_cast<void **>(&m->rstd[l]), sizeof(float) * c.c[l]);
     }
     A(reinterpret_cast<void **>(&m->dyb), sizeof(bf16) * zmax);
-    for (int l = 0; l < 4; ++l)
-        m->wpart_elems = std::max<int64_t>(m->wpart_elems, static_cast<int64_t>(std::max(m->n_sm, 1)) * c.c[l] * 27 *
-                                                               m->dims[l][3]);
+    // per-CTA weight-gradient partials: n_sm CTAs of the halo kernel or the splits of the split-K
+    // GEMM, each of Co x 27 Ci floats
+    for (int l = 0; l < 4; ++l) {
+        const int64_t P = static_cast<int64_t>(B) * m->dims[l][0] * m->dims[l][1] * m->dims[l][2];
+        int bm, mt, nt;
+        const int split = tn_split(c.c[l], 27 * m->dims[l][3], P, bm, mt, nt);
+        m->wpart_elems = std::max<int64_t>(m->wpart_elems, static_cast<int64_t>(std::max(std::max(m->n_sm, 1), split)) *
+                                                               c.c[l] * 27 * m->dims[l][3]);
+    }
     A(reinterpret_cast<void **>(&m->wpart), sizeof(float) * m->wpart_elems);
     A(reinterpret_cast<void **>(&m->dact), sizeof(float) * dact);
     A(reinterpret_cast<void **>(&m->part), sizeof(float) * std::max<int64_t>(part, 2));

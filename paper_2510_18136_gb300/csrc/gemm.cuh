@@ -3,7 +3,8 @@
 //
 //   NT:  C[M][N]  = A[M][K] * B[N][K]^T      (A, B K-contiguous)
 //   TN:  C[M][N] += A[K][M]^T * B[K][N]      (A, B contiguous along M / N; split-K
-//                                             partial sums added atomically)
+//                                             partial sums added atomically, or written
+//                                             per split to a workspace for an ordered sum)
 //
 // Tiles of BM x BN x 32 are staged in shared memory with 16-byte cp.async
 // (zero-filled outside the matrix, double buffered) and fed to
@@ -355,10 +356,16 @@ __global__ void __launch_bounds__(kThreads) gemm_kernel(int M, int N, int K, con
                 for (int e = 0; e < 2; ++e) {
                     if (col + e >= N) continue;
                     float *dst = C + row * ldc + col + e;
-                    if (TRANS)
-                        atomicAdd(dst, acc[i][jn][2 * h + e]);
-                    else
+                    if (TRANS) {
+                        // split-K: with part set, each split writes its own slice part[blockIdx.z][M][N]
+                        // (summed afterwards in split order); otherwise atomically into C
+                        if (part != nullptr)
+                            part[(static_cast<int64_t>(blockIdx.z) * M + row) * N + col + e] = acc[i][jn][2 * h + e];
+                        else
+                            atomicAdd(dst, acc[i][jn][2 * h + e]);
+                    } else {
                         *dst = acc[i][jn][2 * h + e];
+                    }
                 }
             }
 }
