@@ -611,11 +611,28 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel(const __grid_consta
                         dst[1] = c;
                     }
                 } else {
-                    const unsigned short *stg = reinterpret_cast<const unsigned short *>(stg_b);
-                    const int pitch = p.stg_pitch / 2;
-                    for (int i = tid; i < n_sub * n_t; i += kThreads) {
-                        const int k = i / n_t, t = i - k * n_t;
-                        xs[(size_t)k * Tp + t] = widen16(stg[(size_t)k * pitch + stg_off + t], p.dtype);
+                    // any window offset: pairs of 16-bit samples from the staged 32-bit words,
+                    // realigned by a byte permute when the offset is odd (Tp is a multiple of 4)
+                    const uint32_t *w32 = reinterpret_cast<const uint32_t *>(stg_b);
+                    const int wpitch = p.stg_pitch / 4, w0 = stg_off >> 1, odd = stg_off & 1;
+                    const int npair = n_t >> 1;
+                    for (int k = 0; k < n_sub; ++k) {
+                        const uint32_t *row = w32 + (size_t)k * wpitch + w0;
+                        float *dst = xs + (size_t)k * Tp;
+                        for (int q = tid; q < npair; q += kThreads) {
+                            const uint32_t u = odd ? __byte_perm(row[q], row[q + 1], 0x5432) : row[q];
+                            float2 v;
+                            if (p.dtype == 1) {
+                                v = make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xffff0000u));
+                            } else {
+                                v = __half22float2(*reinterpret_cast<const __half2 *>(&u));
+                            }
+                            *reinterpret_cast<float2 *>(dst + 2 * q) = v;
+                        }
+                        if ((n_t & 1) && tid == 0) {
+                            const unsigned short *h = reinterpret_cast<const unsigned short *>(stg_b);
+                            dst[n_t - 1] = widen16(h[(size_t)k * (p.stg_pitch / 2) + stg_off + n_t - 1], p.dtype);
+                        }
                     }
                 }
             }
