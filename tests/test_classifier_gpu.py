@@ -21,6 +21,9 @@ from paper_2510_18136_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 DIMS = cnn.CnnDims(B=4, D=16, H=16, W=16, C0=16, C=(8, 8, 16, 16), F=8)
+# 16- and 32-channel layers on 16^3 and 8^3 volumes run the halo-tile convolution and
+# weight-gradient kernels (2 x 8 x 8 bricks); the 4^3 and 2^3 layers the gathering GEMM
+DIMS_HALO = cnn.CnnDims(B=2, D=16, H=16, W=16, C0=16, C=(32, 32, 16, 16), F=8)
 
 
 @pytest.fixture(scope="module")
@@ -70,11 +73,12 @@ def _rel_l2(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
 
 
-@pytest.mark.parametrize("dropout", [0.0, 0.4])
-def test_loss_and_gradients_match_oracle(native, dropout):
+@pytest.mark.parametrize("dims,dropout", [(DIMS, 0.0), (DIMS, 0.4), (DIMS_HALO, 0.0)])
+def test_loss_and_gradients_match_oracle(native, dims, dropout):
+    DIMS = dims
     rng = np.random.default_rng(11)
     x = rng.standard_normal((DIMS.B, DIMS.D, DIMS.H, DIMS.W, DIMS.C0)).astype(np.float32)
-    labels = np.array([0.0, 1.0, 1.0, 0.0], np.float32)
+    labels = np.array([0.0, 1.0, 1.0, 0.0][:DIMS.B], np.float32)
     p = _init(DIMS, 2)
     clf = _make(native, DIMS, dropout=dropout, seed=1234)
     clf.set_params(p)
@@ -104,7 +108,9 @@ def test_loss_and_gradients_match_oracle(native, dropout):
     clf.close()
 
 
-def test_inference_matches_oracle_eval_mode(native):
+@pytest.mark.parametrize("dims", [DIMS, DIMS_HALO])
+def test_inference_matches_oracle_eval_mode(native, dims):
+    DIMS = dims
     rng = np.random.default_rng(12)
     x = rng.standard_normal((DIMS.B, DIMS.D, DIMS.H, DIMS.W, DIMS.C0)).astype(np.float32)
     p = _init(DIMS, 4)
