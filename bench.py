@@ -94,7 +94,7 @@ def make_cube(native, synth, cfg, seed, device, dtype):
 
 # DRAM bytes (read + write) per 301x301 FP32 launch from the ncu capture summarised in
 # profiles/search_kernel_full_window.md, valid for the kernel source with this sha256 prefix.
-NCU_TRAFFIC = {"sha256_16": "a05ae0d93b5c357a", "bytes": 7.034e9, "workload": (301, 301, "f32")}
+NCU_TRAFFIC = {"sha256_16": "8a2d3c395abe93b5", "bytes": 7.029e9, "workload": (301, 301, "f32")}
 
 
 # DRAM bytes of one imager call (grid_kernel + transform_kernel) from the ncu launch list of the
@@ -119,6 +119,13 @@ def measured_traffic(ny, nx, dtype):
     if digest != NCU_TRAFFIC["sha256_16"] or (ny, nx, dtype) != NCU_TRAFFIC["workload"]:
         return None
     return NCU_TRAFFIC["bytes"]
+
+
+def search_kernel_name(n_t, dtype):
+    """The kernel the library launches for this window: chunks of C samples per lane, the smallest
+    compiled C with 32 C > n_t; FP32 cubes run the barrier-free kernel, 16-bit ones the staged one."""
+    c = next(c for c in (1, 3, 5, 9, 17, 25, 38, 39) if 32 * c >= n_t + 1)
+    return f"search_kernel_pipe<{c}>" if dtype == "f32" else f"search_kernel<{c}, false>"
 
 
 def alg_ops(cfg, plan):
@@ -529,7 +536,7 @@ def main():
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                      "unit": "TFLOP/s", "frac": achieved / peak_ops,
                      "traffic": measured_traffic(cfg.ny, cfg.nx, args.dtype),
-                     "kernel": "search_kernel_pipe<39>" if args.dtype == "f32" else "search_kernel<39, false>",
+                     "kernel": search_kernel_name(cfg.n_t, args.dtype),
                      "kernel_ms": kern_s * 1e3,
                      "ops_per_launch": ops, "peak_basis": f"{n_sm} SM x 128 FP32 lanes x "
                      f"{pk['sm_max_mhz']:.0f} MHz ({pk['source']} max clock)"},

@@ -125,10 +125,11 @@ __host__ __device__ inline SmemLayout smem_layout(const SearchParams &p, int C) 
     return L;
 }
 
-// Chunk sizes (samples per lane) with compiled kernels; odd so that lanes
-// reading consecutive chunks hit distinct shared-memory banks.
-constexpr int kChunks[] = {1, 3, 5, 9, 17, 25, 39};
-constexpr int kNumChunks = 7;
+// Chunk sizes (samples per lane) with compiled kernels.  Odd chunks read one sample at a
+// time (lanes C words apart hit distinct banks); the even chunk 38 (= 2 mod 4) reads and
+// computes sample pairs (64-bit accesses of lanes C words apart are conflict-free).
+constexpr int kChunks[] = {1, 3, 5, 9, 17, 25, 38, 39};
+constexpr int kNumChunks = 8;
 
 inline int pick_chunk(int n_t) {
     for (int i = 0; i < kNumChunks; ++i)

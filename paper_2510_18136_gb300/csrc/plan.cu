@@ -43,6 +43,7 @@ cudaError_t launch_search(int C, const SearchParams &p, int grid, size_t smem, c
         case 9: return launch_search_c9(p, grid, smem, s);
         case 17: return launch_search_c17(p, grid, smem, s);
         case 25: return launch_search_c25(p, grid, smem, s);
+        case 38: return launch_search_c38(p, grid, smem, s);
         case 39: return launch_search_c39(p, grid, smem, s);
         default: return cudaErrorInvalidValue;
     }
@@ -56,6 +57,7 @@ cudaError_t prepare_search(int C, size_t smem) {
         case 9: return prepare_search_c9(smem);
         case 17: return prepare_search_c17(smem);
         case 25: return prepare_search_c25(smem);
+        case 38: return prepare_search_c38(smem);
         case 39: return prepare_search_c39(smem);
         default: return cudaErrorInvalidValue;
     }

@@ -85,6 +85,7 @@ cudaError_t launch_search_c5(const SearchParams &, int, size_t, cudaStream_t);
 cudaError_t launch_search_c9(const SearchParams &, int, size_t, cudaStream_t);
 cudaError_t launch_search_c17(const SearchParams &, int, size_t, cudaStream_t);
 cudaError_t launch_search_c25(const SearchParams &, int, size_t, cudaStream_t);
+cudaError_t launch_search_c38(const SearchParams &, int, size_t, cudaStream_t);
 cudaError_t launch_search_c39(const SearchParams &, int, size_t, cudaStream_t);
 cudaError_t prepare_search_c1(size_t);
 cudaError_t prepare_search_c3(size_t);
@@ -92,5 +93,6 @@ cudaError_t prepare_search_c5(size_t);
 cudaError_t prepare_search_c9(size_t);
 cudaError_t prepare_search_c17(size_t);
 cudaError_t prepare_search_c25(size_t);
+cudaError_t prepare_search_c38(size_t);
 cudaError_t prepare_search_c39(size_t);
 }  // namespace nsfrb

@@ -1,0 +1,7 @@
+// Search kernel instantiation for chunks of 38 samples per lane (windows up to 1215 samples),
+// the sample-pair code path.
+#include "search_impl.cuh"
+
+namespace nsfrb {
+NSFRB_INSTANTIATE_SEARCH(38)
+}  // namespace nsfrb

@@ -1,4 +1,4 @@
-// Search kernel instantiation for chunks of 39 samples per lane (windows up to 1247 samples).
+// Search kernel instantiation for chunks of 39 samples per lane (windows of 1216 to 1247 samples).
 #include "search_impl.cuh"
 
 namespace nsfrb {

@@ -284,6 +284,213 @@ __device__ __forceinline__ int warp_min(int v) {
     return v;
 }
 
+// ------------------------------------------------------------------ even chunks: sample pairs
+//
+// With an even C (C = 2 mod 4, so 64-bit accesses of lanes C words apart are conflict-free)
+// a lane's samples are held as pairs (2m, 2m+1): shared-memory rows are read and P is written
+// 64 bits at a time, and the de-dispersion sums and boxcar differences run as two-lane FP32
+// instructions.  Each lane of a pair op rounds exactly like the scalar op, so every value
+// equals the one-sample-at-a-time computation.
+
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float pget(const float2 *v, int i) { return (i & 1) ? v[i >> 1].y : v[i >> 1].x; }
+__device__ __forceinline__ void pset(float2 *v, int i, float x) {
+    if (i & 1)
+        v[i >> 1].y = x;
+    else
+        v[i >> 1].x = x;
+}
+
+// D[c] += xr[c] (SUB: D[c] -= xr[c]) for c < C, xr = subband row + t0 + s.  For even s the
+// row is read in aligned pairs; for odd s the aligned pairs from xr - 1 are realigned.
+template <int C, bool SUB>
+__device__ __forceinline__ void acc_pairs(float2 (&D)[C / 2], const float *xr, bool odd) {
+    if (!odd) {
+        const float2 *x = reinterpret_cast<const float2 *>(xr);
+#pragma unroll
+        for (int m = 0; m < C / 2; ++m) D[m] = SUB ? sub2(D[m], x[m]) : add2(D[m], x[m]);
+    } else {
+        const float2 *x = reinterpret_cast<const float2 *>(xr - 1);
+        float lo = x[0].y;
+#pragma unroll
+        for (int m = 0; m < C / 2; ++m) {
+            const float2 v = x[m + 1];
+            D[m].x = SUB ? D[m].x - lo : D[m].x + lo;
+            D[m].y = SUB ? D[m].y - v.x : D[m].y + v.x;
+            lo = v.y;
+        }
+    }
+}
+
+// First row of a group: D = sum over subbands k of x_k(t + s_k), subbands in order.
+template <int C>
+__device__ __forceinline__ void dd_first(float2 (&D)[C / 2], const float *xs, int Tp, int n_sub,
+                                         const int32_t *sh, int t0) {
+#pragma unroll
+    for (int m = 0; m < C / 2; ++m) D[m] = make_float2(0.0f, 0.0f);
+#pragma unroll 1
+    for (int k = 0; k < n_sub; ++k) {
+        const int s = sh[k];
+        acc_pairs<C, false>(D, xs + (size_t)k * Tp + t0 + s, s & 1);
+    }
+}
+
+// Next row from the previous one: per changed subband, D = (D + x_k(t + s_new)) - x_k(t + s_old).
+template <int C>
+__device__ __forceinline__ void dd_delta(float2 (&D)[C / 2], const float *xs, int Tp, const int32_t *s_delta,
+                                         int d0, int nd, int t0) {
+#pragma unroll 1
+    for (int e = d0; e < d0 + nd; ++e) {
+        const uint32_t pk = static_cast<uint32_t>(s_delta[e]);
+        const int k = pk & 63u, so = (pk >> 6) & 0x1fffu, sn = pk >> 19;
+        const float *row = xs + (size_t)k * Tp + t0;
+        acc_pairs<C, false>(D, row + sn, sn & 1);
+        acc_pairs<C, true>(D, row + so, so & 1);
+    }
+}
+
+// In-lane prefix Lp[c] = D[0] + ... + D[c-1] for c < C as pairs; returns Lp[C] (the lane
+// total).  Two chains split at an even sample, the second offset by the first's total.
+template <int C>
+__device__ __forceinline__ float prefix_pairs(const float2 (&D)[C / 2], float2 (&Lp)[C / 2]) {
+    constexpr int H1 = 2 * ((C / 2 + 1) / 2);
+    float run = 0.0f, tot = 0.0f;
+    Lp[0].x = 0.0f;
+#pragma unroll
+    for (int c = 0; c < H1; ++c) {
+        run = run + pget(D, c);
+        if (c + 1 < C)
+            pset(Lp, c + 1, run);
+        else
+            tot = run;
+    }
+    if constexpr (C > H1) {
+        float q = 0.0f;
+#pragma unroll
+        for (int j = 0; j < C - H1; ++j) {
+            q = (j == 0) ? pget(D, H1) : q + pget(D, H1 + j);
+            const float v = run + q;
+            if (H1 + 1 + j < C)
+                pset(Lp, H1 + 1 + j, v);
+            else
+                tot = v;
+        }
+    }
+    return tot;
+}
+
+// P[t0 + c] = carry + Lp[c] to shared memory, 64 bits at a time.
+template <int C>
+__device__ __forceinline__ void store_p(float *Pw, int t0, float carry, const float2 (&Lp)[C / 2]) {
+    const float2 cc = make_float2(carry, carry);
+    float2 *dst = reinterpret_cast<float2 *>(Pw + t0);
+#pragma unroll
+    for (int m = 0; m < C / 2; ++m) dst[m] = add2(cc, Lp[m]);
+}
+
+// Halo as pairs: Hh holds h[i] for i < SH, h[0] = the lane total (= Lp[C]) and
+// h[i] = total + the next lane's Lp[i] (NaN on the last lane), so that the extended in-lane
+// prefix E = (Lp[0..C), h[0..SH)) pairs up as (E[2j], E[2j+1]).
+template <int C, int SH>
+__device__ __forceinline__ void halo_pairs(const float2 (&Lp)[C / 2], float tot, int lane, float2 (&Hh)[SH / 2]) {
+    Hh[0].x = tot;
+#pragma unroll
+    for (int i = 1; i < SH; ++i) {
+        const float v = __shfl_down_sync(kFull, pget(Lp, i), 1);
+        pset(Hh, i, (lane == 31) ? qnan() : tot + v);
+    }
+}
+
+template <int C, int SH>
+__device__ __forceinline__ float2 ext_pair(const float2 (&Lp)[C / 2], const float2 (&Hh)[SH / 2], int j) {
+    return (j < C / 2) ? Lp[j] : Hh[j - C / 2];
+}
+template <int C, int SH>
+__device__ __forceinline__ float ext_at(const float2 (&Lp)[C / 2], const float2 (&Hh)[SH / 2], int i) {
+    return (i < C) ? pget(Lp, i) : pget(Hh, i - C);
+}
+
+// In-lane width W <= SH: W = 1 is the de-dispersed sample itself; an even W is the difference
+// of extended prefix pairs W / 2 apart.
+template <int C, int SH, int W>
+__device__ __forceinline__ float small_max_pk(const float2 (&D)[C / 2], const float2 (&Lp)[C / 2],
+                                              const float2 (&Hh)[SH / 2]) {
+    static_assert(W == 1 || W % 2 == 0, "in-lane widths are 1 or even");
+    float acc[4] = {neg_inf(), neg_inf(), neg_inf(), neg_inf()};
+#pragma unroll
+    for (int m = 0; m < C / 2; ++m) {
+        float2 b;
+        if constexpr (W == 1)
+            b = D[m];
+        else
+            b = sub2(ext_pair<C, SH>(Lp, Hh, m + W / 2), ext_pair<C, SH>(Lp, Hh, m));
+        acc[m & 3] = fmax3(acc[m & 3], b.x, b.y);
+    }
+    return fmaxf(fmaxf(acc[0], acc[1]), fmaxf(acc[2], acc[3]));
+}
+
+template <int C, int SH, int W>
+__device__ __forceinline__ int small_find_pk_w(const float2 (&D)[C / 2], const float2 (&Lp)[C / 2],
+                                               const float2 (&Hh)[SH / 2], float inv, float target, int t0) {
+    int found = INT_MAX;
+#pragma unroll
+    for (int c = C - 1; c >= 0; --c) {
+        const float b = (W == 1) ? pget(D, c) : ext_at<C, SH>(Lp, Hh, c + W) - ext_at<C, SH>(Lp, Hh, c);
+        if (b * inv == target) found = t0 + c;
+    }
+    return found;
+}
+
+template <int C, int SH>
+__device__ __forceinline__ int small_find_pk(int w, const float2 (&D)[C / 2], const float2 (&Lp)[C / 2],
+                                             const float2 (&Hh)[SH / 2], float inv, float target, int t0) {
+    switch (w) {
+        case 1: return small_find_pk_w<C, SH, 1>(D, Lp, Hh, inv, target, t0);
+        case 2: if constexpr (2 <= SH) return small_find_pk_w<C, SH, 2>(D, Lp, Hh, inv, target, t0); break;
+        case 4: if constexpr (4 <= SH) return small_find_pk_w<C, SH, 4>(D, Lp, Hh, inv, target, t0); break;
+        case 8: if constexpr (8 <= SH) return small_find_pk_w<C, SH, 8>(D, Lp, Hh, inv, target, t0); break;
+        case 16: if constexpr (16 <= SH) return small_find_pk_w<C, SH, 16>(D, Lp, Hh, inv, target, t0); break;
+        default: break;
+    }
+    return INT_MAX;
+}
+
+// Lane-strided P as pairs: Ps[m] = (P[64 m + lane], P[64 m + 32 + lane]).
+template <int C>
+__device__ __forceinline__ void load_ps(const float *Pw, int lane, float2 (&Ps)[C / 2]) {
+#pragma unroll
+    for (int m = 0; m < C / 2; ++m) Ps[m] = make_float2(Pw[64 * m + lane], Pw[64 * m + 32 + lane]);
+}
+
+// Width 32 M, M < C: B = Ps[i + M] - Ps[i] over i < C - M; pairs for even M.
+template <int C, int M>
+__device__ __forceinline__ float large_max_pk(const float2 (&Ps)[C / 2]) {
+    if constexpr (M % 2 == 0) {
+        float acc[4] = {neg_inf(), neg_inf(), neg_inf(), neg_inf()};
+#pragma unroll
+        for (int m = 0; m < (C - M) / 2; ++m) {
+            const float2 b = sub2(Ps[m + M / 2], Ps[m]);
+            acc[m & 3] = fmax3(acc[m & 3], b.x, b.y);
+        }
+        return fmaxf(fmaxf(acc[0], acc[1]), fmaxf(acc[2], acc[3]));
+    } else {
+        return tree_max<C - M>([&](int i) { return pget(Ps, i + M) - pget(Ps, i); });
+    }
+}
+
 // ------------------------------------------------------------------ one warp, one pixel
 
 // The search of one warp over the distinct DM rows [u_lo, u_hi) of one pixel whose
@@ -479,11 +686,198 @@ if constexpr (FULL) {                                                           
     return PixRec{bsnr, bu, bwi, bt};
 }
 
+// Warp sum scan of the lane totals: the prefix P at this lane's first sample.
+__device__ __forceinline__ float lane_carry(float tot, int lane) {
+    float inc = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const float y = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o) inc += y;
+    }
+    float carry = __shfl_up_sync(kFull, inc, 1);
+    return (lane == 0) ? 0.0f : carry;
+}
+
+// Even chunks: the earliest sample whose boxcar of width index wi reaches `target`, from the
+// row's D (in-lane widths) or its P in shared memory (lane-strided and generic widths),
+// evaluated with the operations of the maximum pass.  Returns the minimum over the warp.
+template <int C>
+__device__ __forceinline__ int find_t_even(const SearchParams &p, const float2 (&D)[C / 2], const float *Pw, int wi,
+                                           float inv, float target, int L, int lane, bool masked) {
+    constexpr int SH = (C < kSmallMax) ? C : kSmallMax;
+    const int w = p.widths[wi];
+    int t;
+    if (masked || p.wclass[wi] == WC_GENERIC) {
+        const int tl = masked ? max(0, L - w - p.new_blk + 1) : 0;
+        t = generic_find(Pw, w, L, tl, lane, inv, target);
+    } else if (p.wclass[wi] == WC_SMALL) {
+        float2 Lp[C / 2];
+        float2 Hh[SH / 2];
+        const float tot = prefix_pairs<C>(D, Lp);
+        halo_pairs<C, SH>(Lp, tot, lane, Hh);
+        t = small_find_pk<C, SH>(w, D, Lp, Hh, inv, target, lane * C);
+    } else {
+        float Ps[C];
+#pragma unroll
+        for (int i = 0; i < C; ++i) Ps[i] = Pw[32 * i + lane];
+        t = large_find<C>(w >> 5, Ps, inv, target, lane);
+    }
+    return warp_min(t);
+}
+
+// search_rows for even chunks (sample pairs, see above).
+template <int C, bool FULL>
+__device__ __forceinline__ PixRec search_rows_even(const SearchParams &p, const float *xs, float *Pw,
+                                                   const float *s_inv, const int32_t *s_info,
+                                                   const int32_t *s_delta, const int32_t *s_shift, int u_lo,
+                                                   int u_hi, int64_t pix, int lane) {
+    static_assert(C % 2 == 0, "even chunks only");
+    constexpr int SH = (C < kSmallMax) ? C : kSmallMax;
+    const int n_sub = p.n_sub, n_t = p.n_t, Tp = p.Tp;
+    const int t0 = lane * C;
+    const bool masked = p.new_blk > 0;
+    float bsnr = neg_inf();
+    int bu = -1, bwi = -1, bt = -1;
+    float2 D[C / 2];
+#pragma unroll 1
+    for (int u = u_lo; u < u_hi; ++u) {
+        const int32_t *info = s_info + u * kInfo;
+        if (u == u_lo)
+            dd_first<C>(D, xs, Tp, n_sub, s_shift + u * n_sub, t0);
+        else
+            dd_delta<C>(D, xs, Tp, s_delta, info[UI_DOFF], info[UI_ND], t0);
+        const int L = n_t - info[UI_SMAX];
+
+        float ls = neg_inf();
+        int lw = -1;
+        auto write_full = [&](int wi, float s, int t) {
+            if (lane == 0) {
+                const int fd = info[UI_FIRST_D], ndm = info[UI_N_D];
+                for (int d = fd; d < fd + ndm; ++d) {
+                    const int64_t o = (pix * p.n_dm + d) * p.n_w + wi;
+                    p.full_snr[o] = s;
+                    p.full_t[o] = static_cast<int16_t>(t == INT_MAX ? -1 : t);
+                }
+            }
+        };
+        {
+            float2 Lp[C / 2];
+            const float tot = prefix_pairs<C>(D, Lp);
+            store_p<C>(Pw, t0, lane_carry(tot, lane), Lp);
+            if (!masked && p.has_small) {
+                // power-of-two widths <= min(C, 16) in-lane; ascending width order with a
+                // strict '>' keeps the smallest width index on ties
+                float2 Hh[SH / 2];
+                halo_pairs<C, SH>(Lp, tot, lane, Hh);
+#define NSFRB_SMALL_PK(J)                                                                                 \
+    if constexpr (pow2_class(C, J) == WC_SMALL) {                                                        \
+        const int wi = p.pow2_wi[J];                                                                      \
+        const float m = small_max_pk<C, SH, (1 << J)>(D, Lp, Hh);                                        \
+        const float s = (wi >= 0) ? m * s_inv[wi < 0 ? 0 : wi] : neg_inf();                             \
+        if (s > ls) {                                                                                     \
+            ls = s;                                                                                       \
+            lw = wi;                                                                                      \
+        }                                                                                                 \
+        if constexpr (FULL) {                                                                             \
+            if (wi >= 0) {                                                                                \
+                const float mw = warp_max(m), sw = mw * s_inv[wi];                                       \
+                int t = INT_MAX;                                                                          \
+                if (mw != neg_inf()) t = warp_min(small_find_pk_w<C, SH, (1 << J)>(D, Lp, Hh, s_inv[wi], sw, t0)); \
+                write_full(wi, sw, t);                                                                    \
+            }                                                                                             \
+        }                                                                                                 \
+    }
+                NSFRB_SMALL_PK(0) NSFRB_SMALL_PK(1) NSFRB_SMALL_PK(2) NSFRB_SMALL_PK(3) NSFRB_SMALL_PK(4)
+#undef NSFRB_SMALL_PK
+            }
+        }
+        __syncwarp();
+        if (!masked && p.has_large) {
+            float2 Ps[C / 2];
+            load_ps<C>(Pw, lane, Ps);
+#define NSFRB_LARGE_PK(J)                                                                                 \
+    if constexpr (pow2_class(C, J) == WC_LARGE) {                                                        \
+        const int wi = p.pow2_wi[J];                                                                      \
+        const float m = large_max_pk<C, ((1 << J) >> 5)>(Ps);                                            \
+        const float s = (wi >= 0) ? m * s_inv[wi < 0 ? 0 : wi] : neg_inf();                             \
+        if (s > ls) {                                                                                     \
+            ls = s;                                                                                       \
+            lw = wi;                                                                                      \
+        }                                                                                                 \
+        if constexpr (FULL) {                                                                             \
+            if (wi >= 0) {                                                                                \
+                const float mw = warp_max(m), sw = mw * s_inv[wi];                                       \
+                int t = INT_MAX;                                                                          \
+                if (mw != neg_inf()) t = find_t_even<C>(p, D, Pw, wi, s_inv[wi], sw, L, lane, false);    \
+                write_full(wi, sw, t);                                                                    \
+            }                                                                                             \
+        }                                                                                                 \
+    }
+            NSFRB_POW2(NSFRB_LARGE_PK)
+#undef NSFRB_LARGE_PK
+        }
+        // every other width (and every width of a masked search) from shared memory
+        const int n_gen = masked ? p.n_w : p.n_gen;
+#pragma unroll 1
+        for (int g = 0; g < n_gen; ++g) {
+            const int wi = masked ? g : p.gen_wi[g];
+            const int w = p.widths[wi];
+            const int tl = masked ? max(0, L - w - p.new_blk + 1) : 0;
+            const float m = generic_max(Pw, w, L, tl, lane);
+            const float s = m * s_inv[wi];
+            if (s > ls || (s == ls && wi < lw)) {
+                ls = s;
+                lw = wi;
+            }
+            if constexpr (FULL) {
+                const float mw = warp_max(m), sw = mw * s_inv[wi];
+                int t = INT_MAX;
+                if (mw != neg_inf()) t = warp_min(generic_find(Pw, w, L, tl, lane, s_inv[wi], sw));
+                write_full(wi, sw, t);
+            }
+        }
+
+        // warp arg-max over (S/N, width index), only when some lane beats the warp's best
+        if (__any_sync(kFull, ls > bsnr)) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float os = __shfl_xor_sync(kFull, ls, o);
+                const int ow = __shfl_xor_sync(kFull, lw, o);
+                if (os > ls || (os == ls && ow < lw && ow >= 0)) {
+                    ls = os;
+                    lw = ow;
+                }
+            }
+            if (ls > bsnr) {
+                // earliest sample reaching this S/N, re-evaluated with the same operations
+                const int t = find_t_even<C>(p, D, Pw, lw, s_inv[lw], ls, L, lane, masked);
+                bsnr = ls;
+                bu = u;
+                bwi = lw;
+                bt = t;
+            }
+        }
+        __syncwarp();
+    }
+    return PixRec{bsnr, bu, bwi, bt};
+}
+
+// Per-warp row search for chunk size C (pairs for even C).
+template <int C, bool FULL>
+__device__ __forceinline__ PixRec search_rows_any(const SearchParams &p, const float *xs, float *Pw, const float *s_inv,
+                                                  const int32_t *s_info, const int32_t *s_delta,
+                                                  const int32_t *s_shift, int u_lo, int u_hi, int64_t pix,
+                                                  int lane) {
+    if constexpr (C % 2 == 0)
+        return search_rows_even<C, FULL>(p, xs, Pw, s_inv, s_info, s_delta, s_shift, u_lo, u_hi, pix, lane);
+    else
+        return search_rows<C, FULL>(p, xs, Pw, s_inv, s_info, s_delta, s_shift, u_lo, u_hi, pix, lane);
+}
+
 // ------------------------------------------------------------------ the kernel
 
 template <int C, bool FULL>
 __global__ void __launch_bounds__(kThreads, 1) search_kernel(const __grid_constant__ SearchParams p) {
-    constexpr int SH = (C < kSmallMax) ? C : kSmallMax;
     extern __shared__ __align__(128) unsigned char smem[];
     const SmemLayout lay = smem_layout(p, C);
     int32_t *s_table = reinterpret_cast<int32_t *>(smem + lay.table);
@@ -559,7 +953,6 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel(const __grid_consta
     const int u_lo = (warp * n_ua) / kWarps;
     const int u_hi = ((warp + 1) * n_ua) / kWarps;
     float *Pw = s_pbuf + (size_t)warp * 32 * C;
-    const int t0 = lane * C;
 
     uint32_t phase[2] = {0u, 0u};
     if (p.stage != 0 && tid == 0 && blockIdx.x < n_items) issue(blockIdx.x, 0);
@@ -676,7 +1069,7 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel(const __grid_consta
         // ---- per-warp search over its rows
         PixRec wr{neg_inf(), -1, -1, -1};
         if (!bad_pixel)
-            wr = search_rows<C, FULL>(p, xs, Pw, s_inv, s_info, s_delta, s_shift, u_lo, u_hi, pix, lane);
+            wr = search_rows_any<C, FULL>(p, xs, Pw, s_inv, s_info, s_delta, s_shift, u_lo, u_hi, pix, lane);
         const float bsnr = wr.snr;
         const int bu = wr.dm_idx, bwi = wr.w_idx, bt = wr.t_idx;
         // FULL mode: DM rows that have no trial at all
@@ -805,8 +1198,8 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel_pipe(const __grid_c
         const int g = (warp + i) % kWarps;
         const int u_lo = (g * n_ua) / kWarps, u_hi = ((g + 1) * n_ua) / kWarps;
         const int64_t pix = item_pixel(it);
-        const PixRec wr = search_rows<C, false>(p, s_xs + (size_t)b * n_sub * Tp, Pw, s_inv + b * kMaxW, s_info,
-                                                s_delta, s_shift, u_lo, u_hi, pix, lane);
+        const PixRec wr = search_rows_any<C, false>(p, s_xs + (size_t)b * n_sub * Tp, Pw, s_inv + b * kMaxW,
+                                                    s_info, s_delta, s_shift, u_lo, u_hi, pix, lane);
         // publish; this warp's reads of buffer b are done before the copy that refills it
         fence_proxy_async();
         int last = 0;
