@@ -21,6 +21,21 @@ extern "C" {
 nsfrb_status nsfrb_dbg_gemm(int32_t tn, int32_t M, int32_t N, int32_t K, const void *d_a, const void *d_b,
                             float *d_c, void *stream);
 
+/* One 3x3x3 convolution of the classifier (Sec. 2.3; zero padding 1) on device buffers,
+ * asynchronous on `stream`:
+ *   y[b][z][y][x][co] = sum over taps (dz, dy, dx) and ci of
+ *                       w[co][(dz * 3 + dy) * 3 + dx][ci] * x[b][z + dz - 1][y + dy - 1][x + dx - 1][ci]
+ * x: BF16 [B][D][H][W][CI] (channels last), w: BF16 [CO][27][CI], y: FP32 [B][D][H][W][CO].
+ * d_part (may be NULL): per 128-voxel brick of the kernel that ran, the column sums of y and
+ * of y^2 ([brick][2][CO], FP32); d_err: device int32 that a kernel ORs error bits into.
+ * path 0: the library's choice (tcgen05 kernel, else the mma.sync halo kernel);
+ * path 1: the mma.sync halo kernel only; path 2: the tcgen05 kernel only.
+ * EINVAL when the requested path has no kernel for the shape, channels or shared memory.
+ * *h_used (host int32, may be NULL) receives 1 (halo kernel) or 2 (tcgen05 kernel). */
+nsfrb_status nsfrb_dbg_conv3(int32_t path, int32_t B, int32_t D, int32_t H, int32_t W, int32_t CI, int32_t CO,
+                             const void *d_x, const void *d_w, float *d_y, float *d_part, int32_t *d_err,
+                             int32_t *h_used, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

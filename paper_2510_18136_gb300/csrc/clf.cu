@@ -22,6 +22,7 @@
 #include <cuda_bf16.h>
 
 #include "conv3.cuh"
+#include "conv3_tc.cuh"
 #include "gemm.cuh"
 #include "nsfrb_debug.h"
 #include "plan_internal.h"
@@ -522,6 +523,9 @@ nsfrb_status clf_fail(nsfrb_status st, const std::string &msg) {
     return st;
 }
 
+// Device word of error bits latched by the kernels (after the loss in the same allocation).
+int *clf_err(nsfrb_clf_s *c) { return reinterpret_cast<int *>(c->loss + 1); }
+
 constexpr int kWinPerBlock = 64;     // pooling windows per block of the batch-norm backward partials
 
 // C[M][N] = A[M][K] B[N][K]^T; with gx.x set, A is the im2col matrix of gx (gathered).
@@ -625,6 +629,44 @@ int conv3_occupancy(int max_smem) {
     return occ;
 }
 
+// 3x3x3 convolution on tcgen05 when the volume divides into 1 x 16 x 8 bricks and the shared
+// memory fits.  The grid is the CTAs that shared memory lets reside on every SM, at most
+// 512 / (the CTA's tensor-memory columns) so that no CTA waits for tensor memory.  Returns
+// false when it does not apply (nothing launched).
+template <int CI, int CO>
+bool conv3_tc_try(const bf16 *x, const bf16 *w, float *y, float *part, int B, int D, int H, int W, int max_smem,
+                  int n_sm, int *d_err, cudaStream_t s, cudaError_t &err) {
+    using S = conv3tc::Shape<CI, CO>;
+    if (H % conv3tc::BY || W % conv3tc::BX || W < 16 || D < 4) return false;
+    static int blocks_per_sm = 0;   // per instance: attribute set and residency computed once; -1: not usable
+    if (blocks_per_sm == 0) {
+        blocks_per_sm = -1;
+        int dev = 0, sm_smem = 0, reserved = 0;
+        cudaGetDevice(&dev);
+        if (S::smem <= static_cast<size_t>(max_smem) &&
+            cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) == cudaSuccess &&
+            cudaFuncSetAttribute(conv3tc::conv3_tc_kernel<CI, CO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(S::smem)) == cudaSuccess) {
+            cudaFuncAttributes fa{};
+            if (cudaFuncGetAttributes(&fa, conv3tc::conv3_tc_kernel<CI, CO>) == cudaSuccess) {
+                const int by_smem = sm_smem / static_cast<int>(S::smem + reserved);
+                const int warp_regs = (fa.numRegs * 32 + 255) / 256 * 256;   // allocation unit: 256 per warp
+                const int by_regs = 65536 / (warp_regs * (conv3tc::kThreads / 32));
+                blocks_per_sm = std::min(std::min(by_smem, by_regs), static_cast<int>(512u / S::cols));
+                if (blocks_per_sm < 1) blocks_per_sm = -1;
+            }
+        }
+        cudaGetLastError();
+    }
+    if (blocks_per_sm < 1) return false;
+    const int n_bricks = B * D * (H / conv3tc::BY) * (W / conv3tc::BX);
+    const int grid = std::min(n_bricks, blocks_per_sm * n_sm);
+    conv3tc::conv3_tc_kernel<CI, CO><<<grid, conv3tc::kThreads, S::smem, s>>>(x, w, y, part, D, H, W, n_bricks, d_err);
+    err = cudaGetLastError();
+    return true;
+}
+
 // Two halo buffers unless one buffer keeps more CTAs (warps) resident per SM.
 template <int CI, int CO>
 bool conv3_pair(const bf16 *x, const bf16 *w, float *y, float *part, int B, int D, int H, int W, int max_smem,
@@ -673,9 +715,24 @@ bool wgrad_launch(int CI, int CO, const bf16 *x, const bf16 *dy, float *wpart, i
     return false;
 }
 
+// 3x3x3 convolution by the tcgen05 kernel if it applies, else by the mma.sync halo kernel;
+// false when neither does (nothing launched).  paths: bit 0 allows the halo kernel, bit 1 the
+// tcgen05 kernel; *used tells which ran (1 or 2).
 bool conv3_launch(int CI, int CO, const bf16 *x, const bf16 *w, float *y, float *part, int B, int D, int H, int W,
-                  int max_smem, int n_sm, cudaStream_t s, cudaError_t &err) {
+                  int max_smem, int n_sm, int *d_err, cudaStream_t s, cudaError_t &err, int paths = 3,
+                  int *used = nullptr) {
     err = cudaSuccess;
+    if (used) *used = 2;
+#define NSFRB_CONV3_TC(A, Bc)                                                                          \
+    if (CI == A && CO == Bc && conv3_tc_try<A, Bc>(x, w, y, part, B, D, H, W, max_smem, n_sm, d_err, s, err)) \
+        return true;
+    if (paths & 2) {
+        NSFRB_CONV3_TC(16, 16) NSFRB_CONV3_TC(16, 32) NSFRB_CONV3_TC(16, 64)
+        NSFRB_CONV3_TC(32, 16) NSFRB_CONV3_TC(32, 32) NSFRB_CONV3_TC(32, 64) NSFRB_CONV3_TC(64, 16)
+    }
+#undef NSFRB_CONV3_TC
+    if (used) *used = 1;
+    if (!(paths & 1)) return false;
     if (D % conv3::BZ || H % conv3::BY || W % conv3::BX) return false;
 #define NSFRB_CONV3(A, Bc)                                                                               \
     if (CI == A && CO == Bc) return conv3_pair<A, Bc>(x, w, y, part, B, D, H, W, max_smem, n_sm, s, err);
@@ -704,7 +761,7 @@ nsfrb_status forward(nsfrb_clf_s *c, const bf16 *x, const float *labels, int B, 
         // training: the convolution also leaves the per-tile (128-row) channel sums of y and y^2
         cudaError_t ce;
         if (conv3_launch(Ci, Co, in, c->wb[l], c->y[l], train ? c->part : nullptr, B, D, H, W, c->max_smem, c->n_sm,
-                         s, ce)) {
+                         clf_err(c), s, ce)) {
             if (ce != cudaSuccess) return clf_cuda(c, ce, "conv3");
         } else if (gemm_nt_g<1>(P, Co, 27 * Ci, nullptr, c->wb[l], c->y[l], gemm::make_gather(in, D, H, W, Ci), s,
                                 train ? c->part : nullptr) != NSFRB_OK) {
@@ -774,7 +831,8 @@ nsfrb_status backward(nsfrb_clf_s *c, const bf16 *x, const float *labels, int B,
         if (l > 0) {
             // input gradient: a convolution of dy with the flipped, transposed weights
             cudaError_t ce;
-            if (conv3_launch(Co, Ci, c->dyb, c->wf[l], c->dact, nullptr, B, D, H, W, c->max_smem, c->n_sm, s, ce)) {
+            if (conv3_launch(Co, Ci, c->dyb, c->wf[l], c->dact, nullptr, B, D, H, W, c->max_smem, c->n_sm, clf_err(c), s,
+                             ce)) {
                 if (ce != cudaSuccess) return clf_cuda(c, ce, "conv3 input gradient");
             } else if (gemm_nt_g<1>(P, Ci, 27 * Co, nullptr, c->wf[l], c->dact, gemm::make_gather(c->dyb, D, H, W, Co),
                                     s) != NSFRB_OK) {
@@ -893,12 +951,13 @@ nsfrb_status nsfrb_clf_create(const nsfrb_clf_config *cfg, nsfrb_clf_t *out) {
     A(reinterpret_cast<void **>(&m->dh1), sizeof(float) * B * c.f);
     A(reinterpret_cast<void **>(&m->logit), sizeof(float) * B);
     A(reinterpret_cast<void **>(&m->loss_terms), sizeof(float) * B);
-    A(reinterpret_cast<void **>(&m->loss), sizeof(float));
+    A(reinterpret_cast<void **>(&m->loss), sizeof(float) * 2);   // the loss, then the kernels' error bits
     if (!ok) {
         cudaGetLastError();
         nsfrb_clf_destroy(m);
         return clf_fail(NSFRB_ENOMEM, "classifier device buffers");
     }
+    cudaMemset(m->loss, 0, sizeof(float) * 2);
     cudaMemset(m->params, 0, sizeof(float) * o);
     cudaMemset(m->grads, 0, sizeof(float) * o);
     cudaMemset(m->adam_m, 0, sizeof(float) * o);
@@ -986,10 +1045,18 @@ nsfrb_status nsfrb_clf_train_step(nsfrb_clf_t clf, const void *d_x, const float 
         if ((st = clf_cuda(clf, cudaGetLastError(), "adam")) != NSFRB_OK) return st;
     }
     if (h_loss) {
-        if ((st = clf_cuda(clf, cudaMemcpyAsync(h_loss, clf->loss, sizeof(float), cudaMemcpyDeviceToHost, s),
+        float out[2];
+        if ((st = clf_cuda(clf, cudaMemcpyAsync(out, clf->loss, sizeof(out), cudaMemcpyDeviceToHost, s),
                            "loss copy")) != NSFRB_OK)
             return st;
-        return clf_cuda(clf, cudaStreamSynchronize(s), "train step");
+        if ((st = clf_cuda(clf, cudaStreamSynchronize(s), "train step")) != NSFRB_OK) return st;
+        *h_loss = out[0];
+        int bits = 0;
+        std::memcpy(&bits, &out[1], sizeof(bits));
+        if (bits != 0) {
+            clf->latched = NSFRB_ECUDA;
+            return clf_fail(NSFRB_ECUDA, "a tensor-core convolution wait timed out");
+        }
     }
     return NSFRB_OK;
 }
@@ -1029,6 +1096,26 @@ nsfrb_status nsfrb_clf_cutouts(nsfrb_plan_t plan, const void *d_cube, const floa
         std::sqrt(static_cast<float>(c.n_sub)), reinterpret_cast<const CandRec *>(d_cand), n, plan->d_smax_w,
         plan->d_smax_w + c.n_dm, d, h, w, static_cast<bf16 *>(d_out));
     return cuda_check(plan, cudaGetLastError(), "cutout launch");
+}
+
+nsfrb_status nsfrb_dbg_conv3(int32_t path, int32_t B, int32_t D, int32_t H, int32_t W, int32_t CI, int32_t CO,
+                             const void *d_x, const void *d_w, float *d_y, float *d_part, int32_t *d_err,
+                             int32_t *h_used, void *stream) {
+    if (path < 0 || path > 2 || B < 1 || D < 1 || H < 1 || W < 1 || !d_x || !d_w || !d_y || !d_err)
+        return clf_fail(NSFRB_EINVAL, "bad convolution arguments");
+    int dev = 0, max_smem = 0, n_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t ce = cudaSuccess;
+    int used = 0;
+    const int paths = path == 0 ? 3 : path;
+    if (!conv3_launch(CI, CO, static_cast<const bf16 *>(d_x), static_cast<const bf16 *>(d_w), d_y, d_part, B, D, H,
+                      W, max_smem, n_sm, d_err, static_cast<cudaStream_t>(stream), ce, paths, &used))
+        return clf_fail(NSFRB_EINVAL, "no convolution kernel for this shape and path");
+    if (ce != cudaSuccess) return clf_cuda(nullptr, ce, "convolution launch");
+    if (h_used) *h_used = used;
+    return NSFRB_OK;
 }
 
 nsfrb_status nsfrb_dbg_gemm(int32_t tn, int32_t M, int32_t N, int32_t K, const void *d_a, const void *d_b,

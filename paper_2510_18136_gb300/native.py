@@ -109,6 +109,8 @@ def _load() -> ctypes.CDLL:
         "nsfrb_bin_time": ([P, c_int32, c_int64, c_int32, c_int32, P, P], c_int32),
         "nsfrb_psf_cluster": ([P, c_int32, c_int32, P, c_int32, c_int32, c_float, c_int32, P, P, P], c_int32),
         "nsfrb_dbg_gemm": ([c_int32, c_int32, c_int32, c_int32, P, P, P, P], c_int32),
+        "nsfrb_dbg_conv3": ([c_int32, c_int32, c_int32, c_int32, c_int32, c_int32, c_int32, P, P, P, P, P, P, P],
+                            c_int32),
         "nsfrb_destroy": ([P], None),
         "nsfrb_strerror": ([c_int32], ctypes.c_char_p),
         "nsfrb_last_error": ([], ctypes.c_char_p),

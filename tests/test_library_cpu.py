@@ -28,8 +28,8 @@ def _declared(header):
 
 
 def test_exports_every_declared_symbol(native):
-    names = _declared("nsfrb.h")
-    assert len(names) >= 16
+    names = _declared("nsfrb.h") + _declared("nsfrb_debug.h")
+    assert len(names) >= 16 and "nsfrb_dbg_conv3" in names
     lib = ctypes.CDLL(native.LIB_PATH)
     for n in names:
         assert hasattr(lib, n), n
