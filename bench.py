@@ -52,6 +52,8 @@ def parse():
                     help="imager: run only the imager section (one JSON object) and exit")
     ap.add_argument("--imager-steps", type=int, default=20,
                     help="timed launches of the imager section, one 25-sample block each (0: skip)")
+    ap.add_argument("--stress-steps", type=int, default=5,
+                    help="timed searches of the 512x512 BF16 MAD stress workload (0: skip)")
     ap.add_argument("--seed", type=int, default=0)
     return ap.parse_args()
 
@@ -423,6 +425,56 @@ def imager_section(native, steps: int, seed: int = 0):
                              "sample": f"{len(pairs)} images of the block, FP64 numpy"}}
 
 
+def stress_section(native, synth, steps: int, seed: int = 0):
+    """The stress workload: 512x512 px x 16 sub x 1200 samples stored in BF16, beam-scaled
+    Student-t noise, MAD normalisation per (pixel, subband), 500 injections, 256 DM 0-4000,
+    12 widths; search kernel time by CUDA events, ALU roofline on the definition's operations
+    (the MAD normalisation's own work is not counted)."""
+    import torch
+    import oracle
+    cfg = synth.config_stress()
+    cube = synth.beam_student_noise(cfg, seed + 5, device="cuda", dtype=torch.float32)
+    raw = synth.draw_injections(cfg, 500, seed + 6, dm_range=(0.0, 4000.0), max_width=cfg.n_t)
+    sh = oracle.delay_table(cfg.freq_mhz, raw["dm"])
+    inj = synth.place_injections(raw, sh, cfg.n_t, cfg.n_sub,
+                                 synth.beam_sigma(cfg)[raw["row"] * cfg.nx + raw["col"]])
+    synth.add_injections(cube, cfg, inj, sh)
+    cube = cube.to(torch.bfloat16)
+    torch.cuda.empty_cache()
+    plan = native.Plan(cfg, dtype="bf16", noise="mad")
+    stream = torch.cuda.current_stream()
+    ops, n_unique = alg_ops(cfg, plan)
+    for _ in range(2):
+        plan.search(cube, stream=stream)
+        cand = plan.candidates()
+    times, kern = [], []
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.search(cube, stream=stream)
+        e1.record(stream)
+        cand = plan.candidates()
+        times.append(e0.elapsed_time(e1) / 1e3)
+        kern.append(plan.last_timing()[0] / 1e3)
+    t, tk = statistics.median(times), statistics.median(kern)
+    pk = peaks()
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    peak_ops = n_sm * 128 * pk["sm_max_mhz"] * 1e6
+    alg_bytes = cfg.n_pix * cfg.n_sub * cfg.n_t * 2 + cfg.n_pix * 16
+    plan.close()
+    del cube
+    torch.cuda.empty_cache()
+    return {"workload": f"{cfg.ny}x{cfg.nx} px x {cfg.n_sub} sub x {cfg.n_t} samples BF16, MAD normalisation, "
+                        f"{len(cfg.dm)} DM 0-4000 ({n_unique} distinct rows), {len(cfg.widths)} widths, 500 injections",
+            "ms_per_search": t * 1e3, "trials_per_s": cfg.n_trials / t, "candidates": int(len(cand)),
+            "roofline": {"bound": "alu", "achieved": ops / tk / 1e12, "peak": peak_ops / 1e12, "unit": "TFLOP/s",
+                         "frac": ops / tk / peak_ops, "kernel": f"{search_kernel_name(cfg.n_t, 'bf16')} (MAD normalisation)",
+                         "kernel_ms": tk * 1e3, "ops_per_launch": ops},
+            "hbm": {"achieved_gbs": alg_bytes / tk / 1e9, "frac": alg_bytes / tk / 1e9 / pk["hbm_gbs"],
+                    "bytes_per_launch": alg_bytes},
+            "l2": f"inputs larger than L2 (cube {alg_bytes / 1e9:.1f} GB)"}
+
+
 # ----------------------------------------------------------------------------- GPU arm
 
 def main():
@@ -517,6 +569,9 @@ def main():
     imager = None
     if args.imager_steps > 0 and rank == 0:
         imager = imager_section(native, args.imager_steps, seed=args.seed)
+    stress = None
+    if args.stress_steps > 0 and rank == 0:
+        stress = stress_section(native, synth, args.stress_steps, seed=args.seed)
 
     pk = peaks()
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -550,6 +605,7 @@ def main():
         "serving": serving,
         "classifier": classifier,
         "imager": imager,
+        "stress": stress,
         "clocks": ck,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
