@@ -61,13 +61,16 @@ __device__ __forceinline__ float key2f(uint32_t k) {
     return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
 }
 
-// Exact order statistic of rank `rank` (0-based) of v[0..n) by one warp:
-// four 8-bit radix passes over an order-preserving integer key.
-static __device__ __noinline__ float warp_select(const float *v, int n, int rank, uint32_t *hist) {
+// Exact order statistic of rank `rank` (0-based) of v[0..n) by one warp: 8-bit radix passes
+// over an order-preserving integer key, from the top byte down.  With key16 every key's low 16
+// bits are fixed by its sign (v holds BF16 values widened to FP32: 0 for positive, 0xffff for
+// negative keys), so two passes fix the key.  Returns the key.
+static __device__ __noinline__ uint32_t warp_select_key(const float *v, int n, int rank, uint32_t *hist, bool key16) {
     const int lane = threadIdx.x & 31;
     uint32_t prefix = 0, pmask = 0;
+    const int last = key16 ? 16 : 0;
 #pragma unroll 1
-    for (int shift = 24; shift >= 0; shift -= 8) {
+    for (int shift = 24; shift >= last; shift -= 8) {
         for (int i = lane; i < kHistBins; i += 32) hist[i] = 0;
         __syncwarp();
         for (int i = lane; i < n; i += 32) {
@@ -114,15 +117,29 @@ static __device__ __noinline__ float warp_select(const float *v, int n, int rank
         pmask |= 255u << shift;
         __syncwarp();
     }
-    return key2f(prefix);
+    if (key16) prefix |= (prefix & 0x80000000u) ? 0u : 0xffffu;
+    return prefix;
 }
 
-// Median of v[0..n): middle order statistic, or the mean of the two middle
-// ones for even n.
-static __device__ __noinline__ float warp_median(const float *v, int n, uint32_t *hist) {
-    const float a = warp_select(v, n, (n - 1) / 2, hist);
+// Median of v[0..n): the middle order statistic, or for even n the mean of the two middle
+// ones, the upper found from the lower: it equals the lower when more than n / 2 keys are at
+// most the lower's key, else it is the smallest key above it.
+static __device__ __noinline__ float warp_median(const float *v, int n, uint32_t *hist, bool key16) {
+    const uint32_t ka = warp_select_key(v, n, (n - 1) / 2, hist, key16);
+    const float a = key2f(ka);
     if (n & 1) return a;
-    const float b = warp_select(v, n, n / 2, hist);
+    const int lane = threadIdx.x & 31;
+    uint32_t le = 0, above = 0xffffffffu;
+    for (int i = lane; i < n; i += 32) {
+        const uint32_t key = f2key(v[i]);
+        if (key <= ka)
+            ++le;
+        else
+            above = min(above, key);
+    }
+    le = __reduce_add_sync(kFull, le);
+    above = __reduce_min_sync(kFull, above);
+    const float b = (le >= static_cast<uint32_t>(n / 2) + 1) ? a : key2f(above);
     return 0.5f * (a + b);
 }
 
@@ -1050,10 +1067,10 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel(const __grid_consta
                                            : s_hist) + warp * kHistBins;
             for (int k = warp; k < n_sub; k += kWarps) {
                 float *row = xs + (size_t)k * Tp;
-                const float med = warp_median(row, n_t, hist);
+                const float med = warp_median(row, n_t, hist, p.dtype == 1);
                 for (int t = lane; t < n_t; t += 32) Pw[t] = fabsf(row[t] - med);
                 __syncwarp();
-                const float mad = warp_median(Pw, n_t, hist);
+                const float mad = warp_median(Pw, n_t, hist, false);
                 if (mad == 0.0f) {
                     if (lane == 0) atomicOr(&s_flag[0], ERR_ZERO_MAD);
                 } else {
