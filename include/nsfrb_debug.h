@@ -29,12 +29,21 @@ nsfrb_status nsfrb_dbg_gemm(int32_t tn, int32_t M, int32_t N, int32_t K, const v
  * d_part (may be NULL): per 128-voxel brick of the kernel that ran, the column sums of y and
  * of y^2 ([brick][2][CO], FP32); d_err: device int32 that a kernel ORs error bits into.
  * path 0: the library's choice (tcgen05 kernel, else the mma.sync halo kernel);
- * path 1: the mma.sync halo kernel only; path 2: the tcgen05 kernel only.
+ * path 1: the mma.sync halo kernel only; path 2: the tcgen05 kernel only;
+ * path 3: the tcgen05 kernel with its halo producers stalled, so that its bounded waits run
+ *         out (after about 2 s): it then ORs 4 into *d_err, frees its tensor memory and returns
+ *         without touching y (failure-path test).
  * EINVAL when the requested path has no kernel for the shape, channels or shared memory.
  * *h_used (host int32, may be NULL) receives 1 (halo kernel) or 2 (tcgen05 kernel). */
 nsfrb_status nsfrb_dbg_conv3(int32_t path, int32_t B, int32_t D, int32_t H, int32_t W, int32_t CI, int32_t CO,
                              const void *d_x, const void *d_w, float *d_y, float *d_part, int32_t *d_err,
                              int32_t *h_used, void *stream);
+
+/* The library's bounded device wait, on its own: a kernel waits on an mbarrier that nothing
+ * arrives at, gives up after limit_ms (1..5000) and latches an error bit, which the host reads.
+ * Returns NSFRB_ETIMEOUT when the wait ran out as it must (the device stays usable), NSFRB_OK
+ * if it did not, EINVAL for a bad limit.  Synchronous. */
+nsfrb_status nsfrb_dbg_wait_timeout(int32_t limit_ms);
 
 #ifdef __cplusplus
 }

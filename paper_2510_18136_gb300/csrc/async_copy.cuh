@@ -42,15 +42,20 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, uint32_t 
     return ok != 0;
 }
 
-// Wait for a phase of an mbarrier with a time limit; false on timeout.
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity) {
+// Wait for a phase of an mbarrier for at most limit_ns; false on timeout.
+__device__ __forceinline__ bool mbar_wait_for(unsigned long long *bar, uint32_t parity, unsigned long long limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     while (!mbar_try_wait(bar, parity)) {
-        if (global_ns() - t0 > kWaitNs) return false;
+        if (global_ns() - t0 > limit_ns) return false;
         __nanosleep(128);
     }
     return true;
+}
+
+// Wait for a phase of an mbarrier with the kernels' time limit; false on timeout.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity) {
+    return mbar_wait_for(bar, parity, kWaitNs);
 }
 
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,

@@ -635,7 +635,7 @@ int conv3_occupancy(int max_smem) {
 // false when it does not apply (nothing launched).
 template <int CI, int CO>
 bool conv3_tc_try(const bf16 *x, const bf16 *w, float *y, float *part, int B, int D, int H, int W, int max_smem,
-                  int n_sm, int *d_err, cudaStream_t s, cudaError_t &err) {
+                  int n_sm, int *d_err, cudaStream_t s, cudaError_t &err, int stall = 0) {
     using S = conv3tc::Shape<CI, CO>;
     if (H % conv3tc::BY || W % conv3tc::BX || W < 16 || D < 4) return false;
     static int blocks_per_sm = 0;   // per instance: attribute set and residency computed once; -1: not usable
@@ -662,7 +662,8 @@ bool conv3_tc_try(const bf16 *x, const bf16 *w, float *y, float *part, int B, in
     if (blocks_per_sm < 1) return false;
     const int n_bricks = B * D * (H / conv3tc::BY) * (W / conv3tc::BX);
     const int grid = std::min(n_bricks, blocks_per_sm * n_sm);
-    conv3tc::conv3_tc_kernel<CI, CO><<<grid, conv3tc::kThreads, S::smem, s>>>(x, w, y, part, D, H, W, n_bricks, d_err);
+    conv3tc::conv3_tc_kernel<CI, CO><<<grid, conv3tc::kThreads, S::smem, s>>>(x, w, y, part, D, H, W, n_bricks, d_err,
+                                                                             stall);
     err = cudaGetLastError();
     return true;
 }
@@ -717,16 +718,19 @@ bool wgrad_launch(int CI, int CO, const bf16 *x, const bf16 *dy, float *wpart, i
 
 // 3x3x3 convolution by the tcgen05 kernel if it applies, else by the mma.sync halo kernel;
 // false when neither does (nothing launched).  paths: bit 0 allows the halo kernel, bit 1 the
-// tcgen05 kernel; *used tells which ran (1 or 2).
+// tcgen05 kernel; bit 2 (tests) runs the tcgen05 kernel with stalled producers, so that its
+// waits time out.  *used tells which ran (1 or 2).
 bool conv3_launch(int CI, int CO, const bf16 *x, const bf16 *w, float *y, float *part, int B, int D, int H, int W,
                   int max_smem, int n_sm, int *d_err, cudaStream_t s, cudaError_t &err, int paths = 3,
                   int *used = nullptr) {
     err = cudaSuccess;
     if (used) *used = 2;
+    const int stall = (paths & 4) ? 1 : 0;
 #define NSFRB_CONV3_TC(A, Bc)                                                                          \
-    if (CI == A && CO == Bc && conv3_tc_try<A, Bc>(x, w, y, part, B, D, H, W, max_smem, n_sm, d_err, s, err)) \
+    if (CI == A && CO == Bc &&                                                                          \
+        conv3_tc_try<A, Bc>(x, w, y, part, B, D, H, W, max_smem, n_sm, d_err, s, err, stall))           \
         return true;
-    if (paths & 2) {
+    if (paths & 6) {
         NSFRB_CONV3_TC(16, 16) NSFRB_CONV3_TC(16, 32) NSFRB_CONV3_TC(16, 64)
         NSFRB_CONV3_TC(32, 16) NSFRB_CONV3_TC(32, 32) NSFRB_CONV3_TC(32, 64) NSFRB_CONV3_TC(64, 16)
     }
@@ -1101,7 +1105,7 @@ nsfrb_status nsfrb_clf_cutouts(nsfrb_plan_t plan, const void *d_cube, const floa
 nsfrb_status nsfrb_dbg_conv3(int32_t path, int32_t B, int32_t D, int32_t H, int32_t W, int32_t CI, int32_t CO,
                              const void *d_x, const void *d_w, float *d_y, float *d_part, int32_t *d_err,
                              int32_t *h_used, void *stream) {
-    if (path < 0 || path > 2 || B < 1 || D < 1 || H < 1 || W < 1 || !d_x || !d_w || !d_y || !d_err)
+    if (path < 0 || path > 3 || B < 1 || D < 1 || H < 1 || W < 1 || !d_x || !d_w || !d_y || !d_err)
         return clf_fail(NSFRB_EINVAL, "bad convolution arguments");
     int dev = 0, max_smem = 0, n_sm = 0;
     cudaGetDevice(&dev);
@@ -1109,7 +1113,7 @@ nsfrb_status nsfrb_dbg_conv3(int32_t path, int32_t B, int32_t D, int32_t H, int3
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     cudaError_t ce = cudaSuccess;
     int used = 0;
-    const int paths = path == 0 ? 3 : path;
+    const int paths = path == 0 ? 3 : path == 3 ? 4 : path;
     if (!conv3_launch(CI, CO, static_cast<const bf16 *>(d_x), static_cast<const bf16 *>(d_w), d_y, d_part, B, D, H,
                       W, max_smem, n_sm, d_err, static_cast<cudaStream_t>(stream), ce, paths, &used))
         return clf_fail(NSFRB_EINVAL, "no convolution kernel for this shape and path");

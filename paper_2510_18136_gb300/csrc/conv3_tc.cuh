@@ -32,7 +32,8 @@
 // MMA, two CTAs per SM ~40 (the shared-memory operand read of 5 KB per MMA): N = 32 caps the
 // tensor pipe at about 40 % of its BF16 peak.
 // On a timeout the kernel latches an error bit, every role stops, the MMA warp waits
-// (bounded) for its MMAs in flight and tensor memory is freed.
+// (bounded) for its MMAs in flight and tensor memory is freed.  `stall` (tests only) keeps the
+// producers from ever marking a halo full, so that this path runs on demand.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -149,7 +150,8 @@ __device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
 template <int CI, int CO>
 __global__ void __launch_bounds__(kThreads, 1) conv3_tc_kernel(const bf16 *__restrict__ x, const bf16 *__restrict__ w,
                                                             float *__restrict__ y, float *__restrict__ part, int D,
-                                                            int H, int W, int n_bricks, int *__restrict__ err) {
+                                                            int H, int W, int n_bricks, int *__restrict__ err,
+                                                            int stall) {
     using S = Shape<CI, CO>;
     constexpr int KC = S::KC;
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -299,12 +301,12 @@ __global__ void __launch_bounds__(kThreads, 1) conv3_tc_kernel(const bf16 *__res
             if (j >= NS - 2) {
                 gemm::cp_async_wait<NS - 2>();   // brick `arrived` (this thread's part) has landed
                 dev::fence_proxy_async();
-                mbar_arrive(&hfull[arrived % NS]);
+                if (!stall) mbar_arrive(&hfull[arrived % NS]);
                 ++arrived;
             }
         }
         gemm::cp_async_wait<0>();
-        if (!*fail) {
+        if (!*fail && !stall) {
             dev::fence_proxy_async();
             for (; arrived < n_mine; ++arrived) mbar_arrive(&hfull[arrived % NS]);
         }

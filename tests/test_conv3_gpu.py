@@ -113,3 +113,19 @@ def test_conv3_tc_declines_shapes_it_cannot_tile(native):
     assert st == native.EINVAL
     st, y, _, used = _run(native, 0, x, w, None)       # the library falls back to the halo kernel
     assert st == native.OK and used == 1 and torch.count_nonzero(y).item() == 0
+
+
+def test_conv3_tc_wait_timeout_is_reported_and_recovers(native):
+    """With its halo producers stalled, the tcgen05 kernel's bounded waits run out: it latches
+    the error bit, frees its tensor memory and returns, y untouched; the next launch is normal."""
+    g = torch.Generator().manual_seed(11)
+    x = torch.randn((1, 4, 16, 16, 16), generator=g).to(torch.bfloat16).cuda()
+    w = (torch.randn((32, 27, 16), generator=g) / 20.0).to(torch.bfloat16).cuda()
+    st, y, err, used = _run(native, 3, x, w, None)
+    assert st == native.OK and used == 2
+    assert err & 4
+    assert torch.isnan(y).all()                       # the epilogue never ran
+    st, y, err, _ = _run(native, 2, x, w, None)
+    assert st == native.OK and err == 0
+    ref, mag = _reference(x.cpu(), w.cpu())
+    assert np.all(np.abs(y.cpu().numpy() - ref) <= 27 * 16 * 2.0 ** -23 * mag + 1e-6)
