@@ -209,8 +209,9 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- CPU oracle legs
 
-def oracle_sample_rate(cube_host, cfg, target_s: float, seed: int = 0):
-    """Time the FP64 oracle on a pixel sample sized for about target_s seconds."""
+def oracle_sample_rate(cube_host, cfg, target_s: float, seed: int = 0, n_fixed: int = 0):
+    """Time the FP64 oracle on a pixel sample sized for about target_s seconds (or of n_fixed
+    pixels, one run)."""
     import oracle
     tab = oracle.delay_table(cfg.freq_mhz, cfg.dm, cfg.k_dm_ms, cfg.t_samp_ms)
     rng = np.random.default_rng(seed)
@@ -223,6 +224,11 @@ def oracle_sample_rate(cube_host, cfg, target_s: float, seed: int = 0):
         oracle.search_cube(x, tab, cfg.widths, sigma=sig)
         return time.perf_counter() - t0
 
+    if n_fixed > 0:
+        n = int(min(cfg.n_pix, n_fixed))
+        t = run(n)
+        cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+        return n * len(cfg.dm) * len(cfg.widths) / t, n, t, cores
     n = 256
     t = run(n)
     for _ in range(2):   # calibrate the sample to about target_s seconds
@@ -245,12 +251,15 @@ def reference_arm(args):
     cfg.sigma_pix = synth.psf_sigma()
     import torch
     host = synth.psf_noise(cfg, args.seed)          # CPU generation, same recipe
+    # one sample size, calibrated once, then one oracle run per step: the whole run takes about
+    # two minutes of host time whatever --steps and --warmup are
     per_step = min(20.0, 120.0 / max(1, args.steps + args.warmup))
-    for _ in range(args.warmup):
-        oracle_sample_rate(host, cfg, per_step / 4)
+    _, n_cal, _, _ = oracle_sample_rate(host, cfg, per_step)
+    for k in range(args.warmup):
+        oracle_sample_rate(host, cfg, per_step, seed=1000 + k, n_fixed=n_cal)
     rates, ns = [], []
     for k in range(args.steps):
-        r, n, t, cores = oracle_sample_rate(host, cfg, per_step, seed=k)
+        r, n, t, cores = oracle_sample_rate(host, cfg, per_step, seed=k, n_fixed=n_cal)
         rates.append(r)
         ns.append(n)
     value = statistics.median(rates)
