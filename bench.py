@@ -229,7 +229,7 @@ def oracle_sample_rate(cube_host, cfg, target_s: float, seed: int = 0, n_fixed: 
         t = run(n)
         cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
         return n * len(cfg.dm) * len(cfg.widths) / t, n, t, cores
-    n = 256
+    n = min(256, cfg.n_pix)
     t = run(n)
     for _ in range(2):   # calibrate the sample to about target_s seconds
         n = int(min(cfg.n_pix, max(16, n * target_s / max(t, 1e-3))))

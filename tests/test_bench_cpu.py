@@ -1,0 +1,35 @@
+"""The benchmark's reference arm (the FP64 oracle on the host cores) keeps the one-line JSON
+contract, run on a tiny grid so that it takes seconds."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_reference_arm_prints_one_json_line():
+    env = dict(os.environ, OMP_NUM_THREADS="2")
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--ny", "6",
+                          "--nx", "6", "--steps", "2", "--warmup", "1"], capture_output=True, text=True,
+                         timeout=600, env=env, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.strip().startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "impl", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["unit"] == "trials/s" and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 2
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    assert d["steps"] == 2 and d["warmup"] == 1
+
+
+def test_search_kernel_name_follows_the_chunk_rule():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.search_kernel_name(1200, "f32") == "search_kernel_pipe<38>"
+    assert bench.search_kernel_name(1200, "bf16") == "search_kernel<38, false>"
+    assert bench.search_kernel_name(1247, "f32") == "search_kernel_pipe<39>"
+    assert bench.search_kernel_name(64, "f32") == "search_kernel_pipe<3>"
