@@ -103,6 +103,9 @@ def test_full_window_fp32(native):
     (100, [1, 4, 16, 17, 31, 32, 64, 96, 100]),
     (333, [2, 7, 9, 24, 32, 33, 160, 320, 333]),
     (700, [1, 3, 5, 9, 16, 64, 100, 512, 640, 699]),
+    # the sample-pair chunk (38 per lane): its shortest and longest windows
+    (801, [1, 2, 4, 8, 16, 32, 64, 128, 256, 512, 800, 801]),
+    (1215, [1, 2, 3, 4, 8, 16, 32, 48, 64, 96, 128, 256, 512, 1024, 1215]),
     (1247, [1, 2, 4, 8, 16, 32, 64, 128, 256, 512, 1024, 1216, 1247]),
     (1, [1]),
     (31, [1, 31]),
