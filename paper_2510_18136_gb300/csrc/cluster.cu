@@ -35,7 +35,6 @@ __global__ void __launch_bounds__(kClusterThreads) cluster_kernel(const CandRec 
                                                                  ClusterOut *__restrict__ out) {
     __shared__ float s_sorted[kMaxPsf];
     __shared__ CandRec s_top[kMaxTop];
-    __shared__ float s_red_v[kClusterThreads / 32];
     __shared__ int s_red_i[kClusterThreads / 32];
     __shared__ float s_thr;
     __shared__ float s_score[kMaxTop];
@@ -67,10 +66,7 @@ __global__ void __launch_bounds__(kClusterThreads) cluster_kernel(const CandRec 
                 bi = oi;
             }
         }
-        if (lane == 0) {
-            s_red_v[warp] = bv;
-            s_red_i[warp] = bi;
-        }
+        if (lane == 0) s_red_i[warp] = bi;
         __syncthreads();
         if (tid == 0) {
             int b = -1;
