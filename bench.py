@@ -94,8 +94,8 @@ def make_cube(native, synth, cfg, seed, device, dtype):
     return cube, inj
 
 
-# DRAM bytes (read + write) per 301x301 FP32 launch from the ncu capture summarised in
-# profiles/search_kernel_full_window.md, valid for the kernel source with this sha256 prefix.
+# DRAM bytes (read + write) per 301x301 FP32 launch from an ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum, scaled from a 64x64 launch), valid for the kernel source with this sha256 prefix.
 NCU_TRAFFIC = {"sha256_16": "7c155e588df33d0d", "bytes": 7.030e9, "workload": (301, 301, "f32")}
 
 

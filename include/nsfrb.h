@@ -186,15 +186,21 @@ typedef struct {
  * order statistics); top_k (10 in the paper, <= 32).
  * Outputs (device): d_top[min(top_k, n)] the top candidates by S/N (ties:
  * smaller pixel index first) and one nsfrb_cluster_result at d_result.
- * Score of a cluster: the mean of the members' S/N referred to the central
- * lobe (snr_j / psf_j, psf_j the PSF value at member j's offset from the
- * central candidate) with inverse-variance weights psf_j^2, i.e.
- * sum_j psf_j snr_j / sum_j psf_j^2 (the least-squares source S/N under the
- * PSF template); for a peak-normalised PSF the central candidate enters with
- * psf = 1.  Asynchronous. */
+ * Score of a cluster (the paper says "weighted mean S/N" and gives no
+ * formula), psf_j the PSF value at member j's offset from the central
+ * candidate (1 for the central one of a peak-normalised PSF):
+ *   score_mode NSFRB_CLUSTER_PSF_MEAN (0): the PSF-weighted mean
+ *     sum_j psf_j snr_j / sum_j psf_j;
+ *   score_mode NSFRB_CLUSTER_LSQ (1): the members' S/N referred to the
+ *     central lobe (snr_j / psf_j) averaged with inverse-variance weights
+ *     psf_j^2, sum_j psf_j snr_j / sum_j psf_j^2 (the least-squares source
+ *     S/N under the PSF template).
+ * Highest score wins, the first in top order on ties.  Asynchronous.
+ * EINVAL on a bad size, percentile or score_mode. */
+enum { NSFRB_CLUSTER_PSF_MEAN = 0, NSFRB_CLUSTER_LSQ = 1 };
 nsfrb_status nsfrb_psf_cluster(const nsfrb_candidate *d_cand, int32_t n, int32_t nx, const float *d_psf,
-                               int32_t ph, int32_t pw, float percentile, int32_t top_k, nsfrb_candidate *d_top,
-                               void *d_result, void *stream);
+                               int32_t ph, int32_t pw, float percentile, int32_t top_k, int32_t score_mode,
+                               nsfrb_candidate *d_top, void *d_result, void *stream);
 
 /* ---- search without device allocation -------------------------------------
  * The paper has no counterpart to this call.  It serves callers that cannot
@@ -217,7 +223,14 @@ nsfrb_status nsfrb_psf_cluster(const nsfrb_candidate *d_cand, int32_t n, int32_t
  * plan's tables <= NSFRB_STATIC_MAX_TABLE_WORDS int32 words (EINVAL beyond);
  * candidate output mode only; no re-scoring.  The first call on a device
  * looks up the array's device address there (and sets the kernel's shared
- * memory limit), so make that first call before any stream capture.  Every
+ * memory limit), so make that first call before any stream capture.  The
+ * array is reserved on a device when the library's code for this call is
+ * first loaded there, which with CUDA's default lazy module loading is that
+ * first call, not the library load: make the first call (a tiny plan will
+ * do) before another allocator claims the device's free memory.  Each call
+ * copies the plan's delay tables (at most NSFRB_STATIC_MAX_TABLE_WORDS int32
+ * words) from the plan's pageable host memory into the array, a copy that
+ * blocks the calling thread until it is staged.  Every
  * call shares the one array and overwrites what the previous call left in
  * it: calls whose work overlaps on the GPU (different streams, or different
  * plans at once) race and must be serialised by the caller. */

@@ -31,7 +31,8 @@ __device__ __forceinline__ bool better(float s1, int64_t p1, float s2, int64_t p
 
 __global__ void __launch_bounds__(kClusterThreads) cluster_kernel(const CandRec *__restrict__ cand, int n, int nx,
                                                                  const float *__restrict__ psf, int ph, int pw,
-                                                                 float pct, int top_k, CandRec *__restrict__ top,
+                                                                 float pct, int top_k, int score_mode,
+                                                                 CandRec *__restrict__ top,
                                                                  ClusterOut *__restrict__ out) {
     __shared__ float s_sorted[kMaxPsf];
     __shared__ CandRec s_top[kMaxTop];
@@ -122,10 +123,11 @@ __global__ void __launch_bounds__(kClusterThreads) cluster_kernel(const CandRec 
             if (y < 0 || y >= ph || x < 0 || x >= pw) continue;
             const float v = psf[y * pw + x];
             if (v < s_thr) continue;
-            // mean of the members' S/N referred to the central lobe (snr_j / v) with
-            // inverse-variance weights v^2: sum v snr / sum v^2
+            // NSFRB_CLUSTER_PSF_MEAN: PSF-weighted mean, sum v snr / sum v.
+            // NSFRB_CLUSTER_LSQ: the members' S/N referred to the central lobe (snr_j / v)
+            // with inverse-variance weights v^2, sum v snr / sum v^2.
             num += v * s_top[j].snr;
-            den += v * v;
+            den += (score_mode == NSFRB_CLUSTER_LSQ) ? v * v : v;
         }
         s_score[tid] = den > 0.0f ? num / den : -FLT_MAX;
     }
@@ -160,12 +162,14 @@ using namespace nsfrb;
 
 extern "C" nsfrb_status nsfrb_psf_cluster(const nsfrb_candidate *d_cand, int32_t n, int32_t nx, const float *d_psf,
                                           int32_t ph, int32_t pw, float percentile, int32_t top_k,
-                                          nsfrb_candidate *d_top, void *d_result, void *stream) {
+                                          int32_t score_mode, nsfrb_candidate *d_top, void *d_result,
+                                          void *stream) {
     if (n < 0 || (n > 0 && !d_cand) || !d_psf || ph < 1 || pw < 1 || ph * pw > kMaxPsf || top_k < 1 ||
-        top_k > kMaxTop || !d_top || !d_result || nx < 1 || !(percentile >= 0.0f && percentile <= 100.0f))
+        top_k > kMaxTop || !d_top || !d_result || nx < 1 || !(percentile >= 0.0f && percentile <= 100.0f) ||
+        (score_mode != NSFRB_CLUSTER_PSF_MEAN && score_mode != NSFRB_CLUSTER_LSQ))
         return fail(nullptr, NSFRB_EINVAL, "bad argument");
     cluster_kernel<<<1, kClusterThreads, 0, static_cast<cudaStream_t>(stream)>>>(
-        reinterpret_cast<const CandRec *>(d_cand), n, nx, d_psf, ph, pw, percentile, top_k,
+        reinterpret_cast<const CandRec *>(d_cand), n, nx, d_psf, ph, pw, percentile, top_k, score_mode,
         reinterpret_cast<CandRec *>(d_top), static_cast<ClusterOut *>(d_result));
     return cuda_check(nullptr, cudaGetLastError(), "cluster launch");
 }

@@ -76,7 +76,8 @@ __global__ void __launch_bounds__(kCompactBlock) static_scatter_kernel(const Pix
 }
 
 // Staging scheme for a contiguous cube under this device's shared-memory limit:
-// bulk copies when the rows are 16-byte aligned, plain loads otherwise.
+// bulk copies when the rows are 16-byte aligned, plain loads otherwise.  FP32 cubes with
+// known noise take the barrier-free kernel, as nsfrb_search does, when its layout fits.
 bool static_stage(int C, int max_smem, SearchParams &sp, size_t &smem) {
     const uintptr_t base = reinterpret_cast<uintptr_t>(sp.cube);
     int want = 0;
@@ -87,6 +88,8 @@ bool static_stage(int C, int max_smem, SearchParams &sp, size_t &smem) {
     for (int st : {want, 0}) {
         sp.stage = st;
         sp.stg_pitch = (st == 2) ? static_cast<int32_t>(align_up(static_cast<size_t>(7 + sp.n_t) * 2, 16)) : 0;
+        sp.pipe = (st == 1 && sp.noise_mode == 0 && !sp.full_snr && sp.new_blk == 0) ? 1 : 0;
+        if (sp.pipe && smem_layout(sp, C).total > static_cast<size_t>(max_smem)) sp.pipe = 0;
         const SmemLayout L = smem_layout(sp, C);
         if (L.total <= static_cast<size_t>(max_smem)) {
             smem = L.total;

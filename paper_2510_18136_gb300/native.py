@@ -107,7 +107,8 @@ def _load() -> ctypes.CDLL:
         "nsfrb_clf_load": ([P, ctypes.c_char_p], c_int32),
         "nsfrb_clf_destroy": ([P], None),
         "nsfrb_bin_time": ([P, c_int32, c_int64, c_int32, c_int32, P, P], c_int32),
-        "nsfrb_psf_cluster": ([P, c_int32, c_int32, P, c_int32, c_int32, c_float, c_int32, P, P, P], c_int32),
+        "nsfrb_psf_cluster": ([P, c_int32, c_int32, P, c_int32, c_int32, c_float, c_int32, c_int32, P, P, P],
+                              c_int32),
         "nsfrb_dbg_gemm": ([c_int32, c_int32, c_int32, c_int32, P, P, P, P], c_int32),
         "nsfrb_dbg_conv3": ([c_int32, c_int32, c_int32, c_int32, c_int32, c_int32, c_int32, P, P, P, P, P, P, P],
                             c_int32),
@@ -504,16 +505,21 @@ CLUSTER_DTYPE = np.dtype([("row", "<i4"), ("col", "<i4"), ("dm_idx", "<i4"), ("w
                           ("members", "<u4")])
 
 
+CLUSTER_SCORES = {"psf_mean": 0, "lsq": 1}
+
+
 def psf_cluster(cand: np.ndarray, nx: int, psf: np.ndarray, percentile: float = 90.0, top_k: int = 10,
-                device="cuda", stream=None):
-    """``nsfrb_psf_cluster`` on a candidate list: returns (top list, result record)."""
+                score: str = "psf_mean", device="cuda", stream=None):
+    """``nsfrb_psf_cluster`` on a candidate list: returns (top list, result record).
+    score: "psf_mean" (sum psf snr / sum psf) or "lsq" (sum psf snr / sum psf^2)."""
     d_cand = candidates_to_device(cand, device) if len(cand) else torch.zeros((1, 6), dtype=torch.int32,
                                                                                device=device)
     d_psf = torch.as_tensor(np.ascontiguousarray(psf, dtype=np.float32)).to(device)
     d_top = torch.zeros((top_k, 6), dtype=torch.int32, device=device)
     d_res = torch.zeros(10, dtype=torch.int32, device=device)
     _check(lib.nsfrb_psf_cluster(_ptr(d_cand), len(cand), int(nx), _ptr(d_psf), psf.shape[0], psf.shape[1],
-                                 float(percentile), int(top_k), _ptr(d_top), _ptr(d_res), _stream_handle(stream)),
+                                 float(percentile), int(top_k), CLUSTER_SCORES[score], _ptr(d_top), _ptr(d_res),
+                                 _stream_handle(stream)),
            "nsfrb_psf_cluster")
     torch.cuda.synchronize()
     res = d_res.cpu().numpy().view(CLUSTER_DTYPE)[0]

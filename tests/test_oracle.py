@@ -292,8 +292,33 @@ def test_psf_cluster_hand_example():
                            ("t_idx", "<i4"), ("snr", "<f4")])
     c["row"], c["col"], c["snr"] = [5, 5, 6, 9], [5, 6, 5, 9], [10.0, 9.0, 8.0, 9.5]
     psf = np.array([[0.1, 0.5, 0.1], [0.5, 1.0, 0.5], [0.1, 0.5, 0.1]])
-    top, best, score, mask = postproc.psf_cluster(c, 16, psf, percentile=50.0, top_k=10)
+    top, best, score, mask = postproc.psf_cluster(c, 16, psf, percentile=50.0, top_k=10, score="lsq")
     assert list(top["snr"]) == [10.0, 9.5, 9.0, 8.0]
     assert (int(top["row"][best]), int(top["col"][best])) == (5, 5)
     assert score == pytest.approx(18.5 / 1.5)
     assert mask == 0b1101   # top order: A (10), D (9.5), B (9), C (8); members A, B, C
+
+
+def test_psf_cluster_hand_example_psf_weighted_mean():
+    """Same candidates and mask, score = sum psf*snr / sum psf over members (the PSF-weighted mean):
+    A: (10 + 4.5 + 4)/(1 + .5 + .5) = 9.25;  B (members B, A): (9 + 5)/1.5 = 9.333;
+    C (members C, A): (8 + 5)/1.5 = 8.667;  D alone: 9.5.  A weighted mean never exceeds its
+    largest member, so here the isolated D is the final candidate; with B raised to 9.8,
+    A: (10 + 4.9 + 4)/2 = 9.45 < B: (9.8 + 5)/1.5 = 9.867, and B wins."""
+    from oracle import postproc
+    c = np.zeros(4, dtype=[("row", "<i4"), ("col", "<i4"), ("dm_idx", "<i4"), ("w_idx", "<i4"),
+                           ("t_idx", "<i4"), ("snr", "<f4")])
+    c["row"], c["col"], c["snr"] = [5, 5, 6, 9], [5, 6, 5, 9], [10.0, 9.0, 8.0, 9.5]
+    psf = np.array([[0.1, 0.5, 0.1], [0.5, 1.0, 0.5], [0.1, 0.5, 0.1]])
+    top, best, score, mask = postproc.psf_cluster(c, 16, psf, percentile=50.0, top_k=10)
+    assert (int(top["row"][best]), int(top["col"][best])) == (9, 9)
+    assert score == pytest.approx(9.5)
+    assert mask == 0b0010
+    c["snr"] = [10.0, 9.8, 8.0, 9.5]
+    top, best, score, mask = postproc.psf_cluster(c, 16, psf, percentile=50.0, top_k=10, score="psf_mean")
+    assert list(top["snr"]) == pytest.approx([10.0, 9.8, 9.5, 8.0])
+    assert (int(top["row"][best]), int(top["col"][best])) == (5, 6)
+    assert score == pytest.approx(14.8 / 1.5)
+    assert mask == 0b0011   # B and A
+    with pytest.raises(ValueError):
+        postproc.psf_cluster(c, 16, psf, score="mean")

@@ -63,8 +63,9 @@ def test_timescales_parity_and_wide_pulse(native):
     assert (t1 == t5).all()
 
 
+@pytest.mark.parametrize("score", ["psf_mean", "lsq"])
 @pytest.mark.parametrize("seed", range(6))
-def test_psf_cluster_matches_plain_statement(native, seed):
+def test_psf_cluster_matches_plain_statement(native, seed, score):
     rng = np.random.default_rng(seed)
     n = int(rng.integers(0, 40))
     c = np.zeros(n, dtype=native.CANDIDATE_DTYPE)
@@ -77,20 +78,21 @@ def test_psf_cluster_matches_plain_statement(native, seed):
     psf = np.exp(-0.5 * (((yy - ph // 2) / 1.5) ** 2 + ((xx - pw // 2) / 1.5) ** 2))
     psf += 0.3 * np.exp(-0.5 * ((np.hypot(yy - ph // 2, xx - pw // 2) - 6.0) / 1.0) ** 2)   # a sidelobe ring
     psf = (psf / psf.max()).astype(np.float32)
-    top, res = native.psf_cluster(c, 64, psf, percentile=90.0, top_k=10)
-    rtop, best, score, mask = postproc.psf_cluster(c, 64, psf.astype(np.float64), 90.0, 10)
+    top, res = native.psf_cluster(c, 64, psf, percentile=90.0, top_k=10, score=score)
+    rtop, best, want, mask = postproc.psf_cluster(c, 64, psf.astype(np.float64), 90.0, 10, score=score)
     assert len(top) == len(rtop)
     np.testing.assert_array_equal(top["row"] * 64 + top["col"], rtop["row"] * 64 + rtop["col"])
     assert int(res["final_rank"]) == best
     if best >= 0:
-        assert float(res["weighted_snr"]) == pytest.approx(score, rel=1e-5)
+        assert float(res["weighted_snr"]) == pytest.approx(want, rel=1e-5)
         assert int(res["members"]) == mask
         assert (int(res["row"]), int(res["col"])) == (int(rtop["row"][best]), int(rtop["col"][best]))
 
 
 def test_psf_cluster_picks_central_lobe(native):
     """A bright source seen through a PSF with a sidelobe ring: the search finds the main lobe and
-    sidelobe pixels; clustering names the main lobe."""
+    sidelobe pixels; the least-squares score names the main lobe, and both scores equal the plain
+    statement on the searched candidates."""
     cfg = synth.SearchConfig(ny=48, nx=48, n_t=64, dm=np.array([0.0]), widths=np.array([1, 2, 4], np.int32))
     R = 10
     yy, xx = np.mgrid[-R:R + 1, -R:R + 1]
@@ -106,5 +108,10 @@ def test_psf_cluster_picks_central_lobe(native):
         plan.search(cube.cuda())
         cand = plan.candidates()
     assert len(cand) > 3
-    top, res = native.psf_cluster(cand, cfg.nx, psf, percentile=90.0, top_k=10)
+    top, res = native.psf_cluster(cand, cfg.nx, psf, percentile=90.0, top_k=10, score="lsq")
     assert (int(res["row"]), int(res["col"])) == (r0, c0)
+    for score in ("psf_mean", "lsq"):
+        top, res = native.psf_cluster(cand, cfg.nx, psf, percentile=90.0, top_k=10, score=score)
+        rtop, best, want, mask = postproc.psf_cluster(cand, cfg.nx, psf.astype(np.float64), 90.0, 10, score=score)
+        assert int(res["final_rank"]) == best and int(res["members"]) == mask
+        assert float(res["weighted_snr"]) == pytest.approx(want, rel=1e-5)

@@ -39,14 +39,18 @@ def _cube(cfg, seed):
     return cube
 
 
+def _launch(native, plan, cube, sigma, out, n):
+    st = native.lib.nsfrb_search_static(plan.handle, ctypes.c_void_p(cube.data_ptr()),
+                                        None if sigma is None else ctypes.c_void_p(sigma.data_ptr()),
+                                        ctypes.c_void_p(out.data_ptr()), out.shape[0], ctypes.c_void_p(n.data_ptr()),
+                                        ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == native.OK, native.lib.nsfrb_last_error()
+
+
 def _static_call(native, plan, cube, sigma, cap):
     out = torch.zeros((cap, 6), dtype=torch.int32, device="cuda")
     n = torch.full((1,), -99, dtype=torch.int32, device="cuda")
-    st = native.lib.nsfrb_search_static(plan.handle, ctypes.c_void_p(cube.data_ptr()),
-                                        ctypes.c_void_p(sigma.data_ptr()), ctypes.c_void_p(out.data_ptr()),
-                                        cap, ctypes.c_void_p(n.data_ptr()),
-                                        ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
-    assert st == native.OK, native.lib.nsfrb_last_error()
+    _launch(native, plan, cube, sigma, out, n)
     torch.cuda.synchronize()
     total = int(n.item())
     rows = out[:min(total, cap)].cpu().numpy()
@@ -93,3 +97,51 @@ def test_static_search_capacity_and_limits(native):
                                         ctypes.c_void_p(cube.data_ptr()), 1, ctypes.c_void_p(cube.data_ptr()),
                                         None)
     assert st == native.EINVAL
+
+
+def test_static_search_mad_mode_and_zero_mad_code(native):
+    """Median/MAD normalisation through the fixed scratch equals nsfrb_search's; a constant
+    (pixel, subband) row (zero MAD) is reported as a count of -1."""
+    cfg = synth.config_full_window(9, 11)
+    cfg.threshold = 4.5
+    plan = native.Plan(cfg, dtype="bf16", noise="mad")
+    ref = native.Plan(cfg, dtype="bf16", noise="mad")
+    for seed in (5, 6):
+        cube = _cube(cfg, seed).to(torch.bfloat16).cuda()
+        ref.search(cube)
+        want = ref.candidates()
+        total, got = _static_call(native, plan, cube, None, cap=cfg.n_pix)
+        assert total == len(want) and total > 0
+        for name in ["row", "col", "dm_idx", "w_idx", "t_idx"]:
+            np.testing.assert_array_equal(got[name], want[name])
+        assert (np.abs(got["snr"].astype(np.float64) - want["snr"]) <= parity.tol(want["snr"])).all()
+    bad = _cube(cfg, 7).to(torch.bfloat16).cuda()
+    bad[17, 3, :] = 2.0
+    total, _ = _static_call(native, plan, bad, None, cap=cfg.n_pix)
+    assert total == -1
+    # the next call starts from cleared counters
+    total, got = _static_call(native, plan, _cube(cfg, 5).to(torch.bfloat16).cuda(), None, cap=cfg.n_pix)
+    assert total > 0
+    plan.close()
+    ref.close()
+
+
+def test_static_search_allocates_nothing(native):
+    """Repeated calls leave the device's free memory unchanged (the scratch array is reserved
+    by the first call on the device, before the measurement)."""
+    cfg = synth.config_full_window(13, 17)
+    sigma = torch.full((cfg.n_pix,), synth.psf_sigma() * 4.0, device="cuda")
+    cube = _cube(cfg, 8).cuda()
+    out = torch.zeros((cfg.n_pix, 6), dtype=torch.int32, device="cuda")
+    n = torch.zeros((1,), dtype=torch.int32, device="cuda")
+    plan = native.Plan(cfg)
+    _launch(native, plan, cube, sigma, out, n)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        _launch(native, plan, cube, sigma, out, n)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert int(n.item()) >= 0
+    plan.close()
