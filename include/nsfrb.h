@@ -80,8 +80,16 @@ typedef struct {
     int32_t out_mode;        /* NSFRB_OUT_CANDIDATES / NSFRB_OUT_FULL          */
     float rescore_eps;       /* BF16/F16 only: pixels whose best S/N lies within
                                 +-rescore_eps of the threshold are searched
-                                again from the FP32 cube when one is given;
-                                <= 0 disables re-scoring                        */
+                                again in FP32 (offline: from the FP32 cube
+                                passed to nsfrb_search; serving: from an FP32
+                                copy of the window in pinned host memory);
+                                <= 0 disables re-scoring.  Measured BF16 S/N
+                                errors against the FP64 search of the FP32
+                                input: <= 0.03 with known noise (full-window
+                                and serving workloads), <= 0.08 with MAD
+                                normalisation (512x512 Student-t workload);
+                                use at least the bound of the workload so that
+                                the candidate set equals the FP32 one           */
 } nsfrb_config;
 
 /* One candidate: the pixel's best trial (maximum S/N over DM, width, time;
@@ -247,11 +255,19 @@ nsfrb_status nsfrb_search_static(nsfrb_plan_t plan, const void *d_cube, const fl
  * transposed into the window, and only the trials that end inside the new
  * block are searched (t + w - 1 + smax_d >= n_t - n_blk).  The per-block
  * search runs as a captured CUDA graph.  Subbands missing from
- * present_mask are zero-filled for that block. */
+ * present_mask are zero-filled for that block.
+ * Re-scoring (16-bit storage with cfg.rescore_eps > 0): the stream also keeps
+ * the window in FP32 in pinned host memory (ny*nx*n_sub*n_t*4 bytes, mapped,
+ * written by the device as blocks arrive); after each block the pixels whose
+ * best S/N over the new trials lies within +-rescore_eps of the threshold are
+ * searched again from it in FP32 (same new-trial mask) before the candidate
+ * list is formed. */
 
 /* Admit a stream: allocates the window and block buffers if the device has
- * hbm_budget bytes free beyond what this stream needs (ENOMEM otherwise).
- * n_blk: samples per block (1..n_t). */
+ * hbm_budget bytes free beyond what this stream needs (ENOMEM otherwise;
+ * also ENOMEM if the pinned host window for re-scoring cannot be had).
+ * n_blk: samples per block (1..n_t).  One plan serves one field; concurrent
+ * fields are separate plans (each with its own stream and graph). */
 nsfrb_status nsfrb_stream_open(nsfrb_plan_t plan, int32_t n_blk, size_t hbm_reserve);
 
 /* Bytes of device memory a stream of this plan needs. */

@@ -55,6 +55,8 @@ struct SearchParams {
     int64_t cube_pix0;     // pixel index of the cube pointer's first pixel
     int32_t t_off;         // first window sample inside a row
     const int32_t *t_off_dev;   // if set, t_off is read from device memory
+    int32_t t_wrap;        // > 0: a row is a ring of t_wrap samples, window sample t sits at
+                           // (t_off + t) mod t_wrap (t_off < t_wrap; plain loads only)
     int32_t dtype;         // NSFRB_F32 / BF16 / F16
     int32_t n_sub, n_t;
     int32_t Tp;            // shared-memory row pitch (floats)

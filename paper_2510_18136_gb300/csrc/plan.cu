@@ -110,7 +110,9 @@ bool choose_stage(const nsfrb_plan_s *pl, SearchParams &sp, size_t &smem) {
     const uintptr_t base = reinterpret_cast<uintptr_t>(sp.cube);
     const int n_t = sp.n_t;
     int want = 0;
-    if (sp.dtype == NSFRB_F32) {
+    if (sp.t_wrap > 0) {
+        want = 0;   // ring rows: plain loads with the wrap-around index
+    } else if (sp.dtype == NSFRB_F32) {
         // bulk copies start at the window start: 16-byte aligned only if it is a multiple of 4
         // samples.  A window start kept on the device (serving) moves by new_blk per block.
         const bool start_aligned = sp.t_off_dev ? (sp.new_blk > 0 && sp.new_blk % 4 == 0) : (sp.t_off % 4 == 0);
@@ -195,7 +197,8 @@ nsfrb_status ensure_device(nsfrb_plan_s *pl) {
 // Queue search kernel(s) over pixels [pix0, pix0 + n) of the cube on stream s.
 nsfrb_status queue_search(nsfrb_plan_s *pl, const void *cube, int64_t cube_pix0, int dtype, int64_t row_len,
                           int t_off, const float *sigma, int64_t pix0, int64_t n, const int32_t *pix_list,
-                          const int32_t *n_items_dev, int new_blk, cudaStream_t s, const int32_t *t_off_dev) {
+                          const int32_t *n_items_dev, int new_blk, cudaStream_t s, const int32_t *t_off_dev,
+                          int t_wrap) {
     SearchParams sp;
     base_params(pl, sp);
     sp.cube = cube;
@@ -204,6 +207,7 @@ nsfrb_status queue_search(nsfrb_plan_s *pl, const void *cube, int64_t cube_pix0,
     sp.row_len = row_len;
     sp.t_off = t_off;
     sp.t_off_dev = t_off_dev;
+    sp.t_wrap = t_wrap;
     sp.sigma = sigma;
     sp.pix0 = pix0;
     sp.n_items = n;

@@ -988,7 +988,9 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel(const __grid_consta
             const int64_t row0 = (pix - p.cube_pix0) * n_sub;
             for (int i = tid; i < n_sub * n_t; i += kThreads) {
                 const int k = i / n_t, t = i - k * n_t;
-                xs[(size_t)k * Tp + t] = load_elem(p.cube, (row0 + k) * p.row_len + t_off + t, p.dtype);
+                int tt = t_off + t;
+                if (p.t_wrap > 0 && tt >= p.t_wrap) tt -= p.t_wrap;
+                xs[(size_t)k * Tp + t] = load_elem(p.cube, (row0 + k) * p.row_len + tt, p.dtype);
             }
         } else {
             const bool ok = mbar_wait(&s_bar[sb], phase[sb]);

@@ -38,11 +38,13 @@ constexpr int kTrPix = 32;   // pixels per transpose tile
 // blk [n_blk][n_sub][n_pix] FP32 -> ring rows, both copies; subbands whose
 // bit is clear in *mask are written as zero.  One CTA per (32-pixel tile,
 // subband); the tile is staged through shared memory so that both the reads
-// (along pixels) and the writes (along samples) are contiguous.
+// (along pixels) and the writes (along samples) are contiguous.  With fring
+// (re-score of 16-bit windows) the FP32 values also go to the host-pinned
+// window [n_pix][n_sub][n_t], a ring of n_t samples per row.
 template <typename T>
 __global__ void ingest_kernel(const float *__restrict__ blk, T *__restrict__ ring, int64_t n_pix, int n_sub,
                               int n_blk, int n_t, int64_t ring_len, const int32_t *__restrict__ state,
-                              const uint32_t *__restrict__ mask) {
+                              const uint32_t *__restrict__ mask, float *__restrict__ fring) {
     extern __shared__ float tile[];   // [n_blk][kTrPix + 1]
     const int k = blockIdx.y;
     const int64_t p0 = static_cast<int64_t>(blockIdx.x) * kTrPix;
@@ -62,10 +64,12 @@ __global__ void ingest_kernel(const float *__restrict__ blk, T *__restrict__ rin
         if (p >= n_pix) continue;
         int pos = wpos + t;
         if (pos >= n_t) pos -= n_t;
-        const T v = narrow<T>(tile[t * (kTrPix + 1) + j]);
+        const float f = tile[t * (kTrPix + 1) + j];
+        const T v = narrow<T>(f);
         T *row = ring + (p * n_sub + k) * ring_len;
         row[pos] = v;
         row[pos + n_t] = v;
+        if (fring) fring[(p * n_sub + k) * n_t + pos] = f;
     }
 }
 
@@ -89,6 +93,9 @@ void destroy_stream_state(nsfrb_plan_s *pl) {
     cudaFree(pl->d_ring);
     cudaFree(pl->d_blk);
     cudaFree(pl->d_sstate);
+    if (pl->h_fring) cudaFreeHost(pl->h_fring);
+    pl->h_fring = nullptr;
+    pl->d_fring = nullptr;
     pl->streaming = false;
     cudaGetLastError();
 }
@@ -145,6 +152,24 @@ nsfrb_status nsfrb_stream_open(nsfrb_plan_t plan, int32_t n_blk, size_t hbm_rese
     }
     plan->streaming = true;
     plan->d_mask = reinterpret_cast<uint32_t *>(plan->d_sstate + 4);
+    // re-score of 16-bit windows: the FP32 window in pinned host memory, written by the
+    // ingest kernel and read back only for the pixels near the threshold
+    const bool rescore = c.dtype != NSFRB_F32 && c.rescore_eps > 0.0f;
+    if (rescore) {
+        const size_t fbytes = static_cast<size_t>(n_pix) * c.n_sub * c.n_t * sizeof(float);
+        if (cudaHostAlloc(reinterpret_cast<void **>(&plan->h_fring), fbytes, cudaHostAllocMapped) != cudaSuccess) {
+            cudaGetLastError();
+            plan->h_fring = nullptr;
+            destroy_stream_state(plan);
+            return fail(plan, NSFRB_ENOMEM, "pinned host FP32 window for re-scoring");
+        }
+        std::memset(plan->h_fring, 0, fbytes);
+        if ((st = cuda_check(plan, cudaHostGetDevicePointer(reinterpret_cast<void **>(&plan->d_fring), plan->h_fring, 0),
+                             "host window address"))) {
+            destroy_stream_state(plan);
+            return st;
+        }
+    }
     if ((st = cuda_check(plan, cudaMemset(plan->d_ring, 0, ring_bytes), "ring clear")) ||
         (st = cuda_check(plan, cudaMemset(plan->d_sstate, 0, 64), "state clear")) ||
         (st = cuda_check(plan, cudaStreamCreateWithFlags(&plan->s_stream, cudaStreamNonBlocking), "stream")) ||
@@ -169,21 +194,32 @@ nsfrb_status nsfrb_stream_open(nsfrb_plan_t plan, int32_t n_blk, size_t hbm_rese
     else if (c.dtype == NSFRB_F32)
         ingest_kernel<float><<<tr_grid, 256, tr_smem, s>>>(plan->d_blk, static_cast<float *>(plan->d_ring), n_pix,
                                                            c.n_sub, n_blk, c.n_t, plan->ring_len, plan->d_sstate,
-                                                           plan->d_mask);
+                                                           plan->d_mask, nullptr);
     else if (c.dtype == NSFRB_BF16)
         ingest_kernel<__nv_bfloat16><<<tr_grid, 256, tr_smem, s>>>(
             plan->d_blk, static_cast<__nv_bfloat16 *>(plan->d_ring), n_pix, c.n_sub, n_blk, c.n_t, plan->ring_len,
-            plan->d_sstate, plan->d_mask);
+            plan->d_sstate, plan->d_mask, plan->d_fring);
     else
         ingest_kernel<__half><<<tr_grid, 256, tr_smem, s>>>(plan->d_blk, static_cast<__half *>(plan->d_ring), n_pix,
                                                             c.n_sub, n_blk, c.n_t, plan->ring_len, plan->d_sstate,
-                                                            plan->d_mask);
+                                                            plan->d_mask, plan->d_fring);
     advance_kernel<<<1, 1, 0, s>>>(plan->d_sstate, n_blk, c.n_t);
     cudaMemsetAsync(plan->d_err, 0, sizeof(int32_t), s);
     nsfrb_status qs = NSFRB_OK;
     if (ok)
         qs = queue_search(plan, plan->d_ring, 0, c.dtype, plan->ring_len, 0, nullptr, 0, n_pix, nullptr, nullptr,
                           n_blk, s, plan->d_sstate);
+    if (ok && qs == NSFRB_OK && rescore) {
+        // pixels whose best over the new trials lies within +-rescore_eps of the threshold:
+        // the same masked search again on their FP32 window rows, read from host memory
+        qs = cuda_check(plan,
+                        launch_rescore_select(plan->d_rec, n_pix, c.threshold, c.rescore_eps, plan->d_list,
+                                              plan->d_nlist, s),
+                        "re-score select");
+        if (qs == NSFRB_OK)
+            qs = queue_search(plan, plan->d_fring, 0, NSFRB_F32, c.n_t, 0, nullptr, 0, n_pix, plan->d_list,
+                              plan->d_nlist, n_blk, s, plan->d_sstate, c.n_t);
+    }
     if (ok && qs == NSFRB_OK)
         qs = cuda_check(plan,
                         launch_compact(plan->d_rec, n_pix, c.nx, c.threshold, plan->d_counts, plan->n_blocks,

@@ -11,6 +11,20 @@ import numpy as np
 
 REL = 1e-5
 
+# Stated S/N error of the 16-bit (BF16) storage form against the FP64 search of the FP32 input,
+# |S/N_bf16 - S/N_fp64| <= EPS_ABS + EPS_REL * |S/N|.  Rounding each stored sample to 8
+# significand bits (unit roundoff 2^-8) adds noise of about 2^-8 rms(x) / sqrt(3) per sample to the
+# sums, i.e. about 2e-3 in S/N per trial for unit noise; its maximum over a full-size cube is about
+# 1e-2, and EPS_ABS = 0.03 covers that three times.  With MAD normalisation the median and MAD are
+# taken from the rounded samples, so the normalisation scale, and with it every S/N of the pixel,
+# carries up to about one unit roundoff of relative error: EPS_REL = 2^-7 there.
+BF16_EPS = {"known": (0.03, 0.0), "mad": (0.03, 2.0 ** -7)}
+
+
+def bf16_bound(snr, noise="known"):
+    a, r = BF16_EPS[noise]
+    return a + r * np.abs(np.asarray(snr, dtype=np.float64))
+
 
 def tol(snr, rel=REL):
     return rel * np.maximum(1.0, np.abs(snr))

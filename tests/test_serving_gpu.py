@@ -121,3 +121,52 @@ def test_stream_admission_and_protocol_errors(native):
     plan.stream_poll(timeout_ms=10000)
     assert plan.stream_bytes(8) > 0
     plan.close()
+
+
+@pytest.mark.parametrize("n_blk", [12, 25])
+def test_stream_bf16_rescore_from_fp32_window(native, n_blk):
+    """BF16 window with re-scoring from the pinned FP32 window: pixels whose best over the new
+    trials lies within eps of the threshold carry the FP32 result (FP64 oracle of the FP32
+    values within the FP32 tolerance), the rest the BF16 one, and the candidate set is the FP32
+    oracle's.  A block with a missing subband checks that the FP32 window is zero-filled too."""
+    cfg = synth.SearchConfig(ny=6, nx=7, n_t=96, dm=np.linspace(0, 1500, 20),
+                             widths=np.array([1, 2, 4, 8, 16, 32, 50], np.int32), threshold=5.0)
+    eps = 1.0
+    n_blocks = 12
+    xn = _series(cfg, n_blk * n_blocks, 5).numpy()
+    seen = xn.copy()
+    tab = oracle.delay_table(cfg.freq_mhz, cfg.dm)
+    plan = native.Plan(cfg, dtype="bf16", rescore_eps=eps)
+    plan.stream_open(n_blk)
+    n_rescored = 0
+    for b in range(n_blocks):
+        mask = (1 << 16) - 1
+        if b == 7:
+            mask &= ~(1 << 5)
+            seen[:, 5, b * n_blk:(b + 1) * n_blk] = 0.0
+        blk = torch.from_numpy(xn[:, :, b * n_blk:(b + 1) * n_blk].transpose(2, 1, 0).copy())
+        plan.stream_push(blk.reshape(n_blk, cfg.n_sub, cfg.ny, cfg.nx).contiguous(), present_mask=mask)
+        cand, _ = plan.stream_poll(timeout_ms=10000)
+        end = (b + 1) * n_blk
+        lo = max(0, end - cfg.n_t)
+        window = np.zeros((cfg.n_pix, cfg.n_sub, cfg.n_t), np.float32)
+        window[:, :, cfg.n_t - (end - lo):] = seen[:, :, lo:end]
+        best32 = _window_oracle(cfg, window, n_blk, tab)
+        best16 = _window_oracle(cfg, oracle.bf16_round(window), n_blk, tab)
+        near = np.abs(best16["snr"] - cfg.threshold) <= eps - 1e-3   # clear of the selection edge
+        far = np.abs(best16["snr"] - cfg.threshold) > eps + 1e-3
+        n_rescored += int(near.sum())
+        g_pix = cand["row"].astype(np.int64) * cfg.nx + cand["col"]
+        got = dict(zip(g_pix.tolist(), cand["snr"].tolist()))
+        for p in range(cfg.n_pix):
+            s32, s16 = best32["snr"][p], best16["snr"][p]
+            if near[p] and abs(s32 - cfg.threshold) > parity.tol(s32):
+                assert (p in got) == (s32 > cfg.threshold)
+                if p in got:
+                    assert abs(got[p] - s32) <= parity.tol(s32)
+            elif far[p]:
+                assert (p in got) == (s16 > cfg.threshold)
+                if p in got:
+                    assert abs(got[p] - s16) <= parity.tol(s16)
+    assert n_rescored > 0
+    plan.close()
