@@ -24,6 +24,9 @@ def test_reference_arm_prints_one_json_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 2
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["steps"] == 2 and d["warmup"] == 1
+    # a step is the measured oracle run on its pixel sample
+    assert d["sample_pixels_per_step"] > 0 and d["config"]["injections"] > 0
+    assert d["value"] * d["ms_per_step"] / 1e3 == __import__("pytest").approx(d["sample_trials_per_step"], rel=0.5)
 
 
 def test_search_kernel_name_follows_the_chunk_rule():
