@@ -42,10 +42,11 @@ def n_params(dims: CnnDims) -> int:
 
 def forward_backward(dims: CnnDims, params, x, labels=None, keep=None, p: float = 0.0, train: bool = True,
                      run_mean=None, run_var=None, grads: bool = True, bf16_storage: bool = False):
-    """x: [B, D, H, W, C0] (channels last). Returns dict(loss, logits, grads, run_mean, run_var).
+    """x: [B, D, H, W, C0] (channels last). Returns dict(loss, logits, grads, grad_mag, run_mean,
+    run_var); grad_mag[i] is the sum of the magnitudes of the terms of gradient entry i.
 
-    bf16_storage: round pooled activations and the back-propagated conv-output
-    gradients to bfloat16 where the GPU kernels store them in that format."""
+    bf16_storage: the network with its pooled activations and the back-propagated
+    gradients at the convolution outputs stored in bfloat16 (round to nearest even)."""
     d = dims.c()
     P = np.ascontiguousarray(params, dtype=np.float64)
     X = np.ascontiguousarray(x, dtype=np.float64)
@@ -57,10 +58,11 @@ def forward_backward(dims: CnnDims, params, x, labels=None, keep=None, p: float 
     rv = np.ones(nc) if run_var is None else np.ascontiguousarray(run_var, dtype=np.float64).copy()
     logits = np.empty(dims.B)
     G = np.empty_like(P) if (grads and train and L is not None) else None
-    loss = _load().orc_cnn_forward_backward_ex(ctypes.byref(d), _p(P), _p(X), _p(L), _p(K), float(p),
-                                               int(bool(train)), _p(rm), _p(rv), _p(logits), _p(G),
-                                               int(bool(bf16_storage)))
-    return {"loss": loss, "logits": logits, "grads": G, "run_mean": rm, "run_var": rv}
+    M = np.empty_like(P) if G is not None else None
+    loss = _load().orc_cnn_forward_backward_mag(ctypes.byref(d), _p(P), _p(X), _p(L), _p(K), float(p),
+                                                int(bool(train)), _p(rm), _p(rv), _p(logits), _p(G),
+                                                int(bool(bf16_storage)), _p(M))
+    return {"loss": loss, "logits": logits, "grads": G, "grad_mag": M, "run_mean": rm, "run_var": rv}
 
 
 def philox4x32_10(ctr, key):

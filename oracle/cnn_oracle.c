@@ -146,10 +146,13 @@ static double round_bf16(double v)
  *   the batch mean and the unbiased batch variance are returned in them.
  * logits[B] receive the outputs; returns the loss (0 if labels == NULL).
  */
-double orc_cnn_forward_backward_ex(const orc_cnn_dims *d, const double *params, const double *x,
-                                   const double *labels, const uint8_t *keep, double p, int train,
-                                   double *run_mean, double *run_var, double *logits, double *grads,
-                                   int bf16_storage)
+/* As below; gmag (optional, with grads) receives for every gradient entry the sum of the
+ * magnitudes of the terms that make it up (|terms| of its final sum over samples, voxels or
+ * windows), the scale of the rounding error of any computation of that sum. */
+double orc_cnn_forward_backward_mag(const orc_cnn_dims *d, const double *params, const double *x,
+                                    const double *labels, const uint8_t *keep, double p, int train,
+                                    double *run_mean, double *run_var, double *logits, double *grads,
+                                    int bf16_storage, double *gmag)
 {
     const int B = d->B;
     int dims[5][4];   /* per stage: D, H, W, C of the activation entering conv l (stage 4 = pooled output) */
@@ -269,20 +272,25 @@ double orc_cnn_forward_backward_ex(const orc_cnn_dims *d, const double *params, 
 
     if (grads && train && labels) {
         memset(grads, 0, sizeof(double) * (size_t)n_params_of(d));
+        if (gmag) memset(gmag, 0, sizeof(double) * (size_t)n_params_of(d));
         double *dfeat = (double *)calloc((size_t)nact[4], sizeof(double));
         for (int b = 0; b < B; ++b) {
             double sig = 1.0 / (1.0 + exp(-logits[b]));
             double dz = (sig - labels[b]) / (double)B;
             grads[off_f2b] += dz;
+            if (gmag) gmag[off_f2b] += fabs(dz);
             const double *feat = act[4] + (int64_t)b * fin;
             for (int f = 0; f < F; ++f) {
                 grads[off_f2w + f] += dz * h1d[b * F + f];
+                if (gmag) gmag[off_f2w + f] += fabs(dz * h1d[b * F + f]);
                 double dh = dz * params[off_f2w + f];
                 if (train && keep) dh = keep[b * F + f] ? dh / (1.0 - p) : 0.0;
                 if (h1[b * F + f] <= 0.0) dh = 0.0;
                 grads[off_f1b + f] += dh;
+                if (gmag) gmag[off_f1b + f] += fabs(dh);
                 for (int i = 0; i < fin; ++i) {
                     grads[off_f1w + (int64_t)f * fin + i] += dh * feat[i];
+                    if (gmag) gmag[off_f1w + (int64_t)f * fin + i] += fabs(dh * feat[i]);
                     dfeat[(int64_t)b * fin + i] += dh * params[off_f1w + (int64_t)f * fin + i];
                 }
             }
@@ -317,13 +325,19 @@ double orc_cnn_forward_backward_ex(const orc_cnn_dims *d, const double *params, 
             const double *g = params + off_g[l];
             double *dy = (double *)malloc(sizeof(double) * (size_t)n);
             for (int c = 0; c < cout; ++c) {
-                double sdz = 0.0, sdzh = 0.0;
+                double sdz = 0.0, sdzh = 0.0, mdz = 0.0, mdzh = 0.0;
                 for (int64_t q = 0; q < npos[l]; ++q) {
                     sdz += dz[q * cout + c];
                     sdzh += dz[q * cout + c] * yhat[l][q * cout + c];
+                    mdz += fabs(dz[q * cout + c]);
+                    mdzh += fabs(dz[q * cout + c] * yhat[l][q * cout + c]);
                 }
                 grads[off_b[l] + c] = sdz;
                 grads[off_g[l] + c] = sdzh;
+                if (gmag) {
+                    gmag[off_b[l] + c] = mdz;
+                    gmag[off_g[l] + c] = mdzh;
+                }
                 const double N = (double)npos[l];
                 for (int64_t q = 0; q < npos[l]; ++q) {
                     double v = g[c] * rstd[l][c] / N * (N * dz[q * cout + c] - sdz - yhat[l][q * cout + c] * sdzh);
@@ -332,6 +346,7 @@ double orc_cnn_forward_backward_ex(const orc_cnn_dims *d, const double *params, 
             }
             /* conv backward: weights and input */
             double *dw = grads + off_w[l];
+            double *mw = gmag ? gmag + off_w[l] : NULL;
             const double *w = params + off_w[l];
             double *din = (double *)calloc((size_t)nact[l], sizeof(double));
             for (int b = 0; b < B; ++b)
@@ -351,6 +366,7 @@ double orc_cnn_forward_backward_ex(const orc_cnn_dims *d, const double *params, 
                                             int64_t wi = ((int64_t)co * 27 + (kz * 3 + ky) * 3 + kx) * cin;
                                             for (int ci = 0; ci < cin; ++ci) {
                                                 dw[wi + ci] += go * act[l][ii + ci];
+                                                if (mw) mw[wi + ci] += fabs(go * act[l][ii + ci]);
                                                 din[ii + ci] += go * w[wi + ci];
                                             }
                                         }
@@ -369,6 +385,15 @@ double orc_cnn_forward_backward_ex(const orc_cnn_dims *d, const double *params, 
     free(h1);
     free(h1d);
     return loss;
+}
+
+double orc_cnn_forward_backward_ex(const orc_cnn_dims *d, const double *params, const double *x,
+                                   const double *labels, const uint8_t *keep, double p, int train,
+                                   double *run_mean, double *run_var, double *logits, double *grads,
+                                   int bf16_storage)
+{
+    return orc_cnn_forward_backward_mag(d, params, x, labels, keep, p, train, run_mean, run_var, logits, grads,
+                                        bf16_storage, NULL);
 }
 
 double orc_cnn_forward_backward(const orc_cnn_dims *d, const double *params, const double *x,

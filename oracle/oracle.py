@@ -73,6 +73,9 @@ def _load():
             lib.orc_cnn_forward_backward_ex.argtypes = [P, P, P, P, P, ctypes.c_double, ctypes.c_int,
                                                         P, P, P, P, ctypes.c_int]
             lib.orc_cnn_forward_backward_ex.restype = ctypes.c_double
+            lib.orc_cnn_forward_backward_mag.argtypes = [P, P, P, P, P, ctypes.c_double, ctypes.c_int,
+                                                         P, P, P, P, ctypes.c_int, P]
+            lib.orc_cnn_forward_backward_mag.restype = ctypes.c_double
             lib.orc_philox4x32_10.argtypes = [P, P, P]
             lib.orc_philox4x32_10.restype = None
             lib.orc_dropout_mask.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_uint32,

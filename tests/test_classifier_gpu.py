@@ -1,10 +1,23 @@
 """CUDA classifier kernels vs the FP64 classifier oracle (needs a GPU).
 
-The GPU computes convolutions with BF16 operands (FP32 accumulation) and keeps
-BF16 activations between blocks; the oracle receives the same BF16-rounded
-input and conv weights and computes in FP64.  Tolerances follow from the BF16
-unit roundoff 2^-8 accumulated over four blocks: 3 % relative on the loss and
-6 % relative L2 error per gradient tensor (cosine > 0.995).
+The network is defined with its pooled activations and the back-propagated gradients at the
+convolution outputs stored in bfloat16 (the classifier's BF16 training kernels); the oracle
+computes that network in FP64 (``bf16_storage``), on the same BF16 input and conv weights.
+
+Gradients are compared entry by entry: |g_gpu - g_oracle| <= TAU (M + M_rms), M the sum of the
+magnitudes of the entry's terms (from the oracle) and M_rms the root mean square of M over the
+entry's tensor.  A term is a product of two stored values (or of a stored value and an FP32 one);
+the GPU stores the same BF16 value as the oracle except where its FP32 value and the oracle's FP64
+value fall on two sides of a rounding boundary, and then they differ by one BF16 unit in the last
+place (at most 2^-7 relative): a term moves by at most 2^-6 of its magnitude.  Such one-unit
+differences of the stored inputs of a layer, summed over its 27 C taps, give its outputs an
+absolute error on the scale of typical values, not of the output itself; small values (near the
+ReLU kink, small pooled maxima) therefore carry errors relative to the typical term, which M_rms
+stands for.  A max-pool arg-max taken differently at a near-tie moves one gradient between two
+voxels of a window, a change bounded by those terms' magnitudes.  TAU = 2^-5 covers these;
+FP32 accumulation adds at most K 2^-23 M (K the number of terms), far below.
+Loss and logits are also compared with the plain FP64 network (no storage rounding): the GPU
+must be as close to it as three times the storage rounding's own effect, measured by the oracle.
 """
 import math
 import os
@@ -24,6 +37,9 @@ DIMS = cnn.CnnDims(B=4, D=16, H=16, W=16, C0=16, C=(8, 8, 16, 16), F=8)
 # 16- and 32-channel layers on 16^3 and 8^3 volumes run the halo-tile convolution and
 # weight-gradient kernels (2 x 8 x 8 bricks); the 4^3 and 2^3 layers the gathering GEMM
 DIMS_HALO = cnn.CnnDims(B=2, D=16, H=16, W=16, C0=16, C=(32, 32, 16, 16), F=8)
+# the production network: 32^3 cutouts x 16 subbands, 32-32-64-64 channels, 32 hidden units
+DIMS_PROD = cnn.CnnDims(B=2, D=32, H=32, W=32, C0=16, C=(32, 32, 64, 64), F=32)
+TAU = 2.0 ** -5
 
 
 @pytest.fixture(scope="module")
@@ -73,42 +89,54 @@ def _rel_l2(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
 
 
-@pytest.mark.parametrize("dims,dropout", [(DIMS, 0.0), (DIMS, 0.4), (DIMS_HALO, 0.0)])
+@pytest.mark.parametrize("dims,dropout", [(DIMS, 0.0), (DIMS, 0.4), (DIMS_HALO, 0.0), (DIMS_PROD, 0.0),
+                                          (DIMS_PROD, 0.5)])
 def test_loss_and_gradients_match_oracle(native, dims, dropout):
-    DIMS = dims
     rng = np.random.default_rng(11)
-    x = rng.standard_normal((DIMS.B, DIMS.D, DIMS.H, DIMS.W, DIMS.C0)).astype(np.float32)
-    labels = np.array([0.0, 1.0, 1.0, 0.0][:DIMS.B], np.float32)
-    p = _init(DIMS, 2)
-    clf = _make(native, DIMS, dropout=dropout, seed=1234)
+    x = rng.standard_normal((dims.B, dims.D, dims.H, dims.W, dims.C0)).astype(np.float32)
+    labels = np.array([0.0, 1.0, 1.0, 0.0][:dims.B], np.float32)
+    p = _init(dims, 2)
+    clf = _make(native, dims, dropout=dropout, seed=1234)
     clf.set_params(p)
     xb = torch.from_numpy(x).to(torch.bfloat16).cuda()
     loss = clf.train_step(xb, torch.from_numpy(labels).cuda(), update=False)
-    g = clf.grads()
-    keep = cnn.dropout_mask(DIMS.B, DIMS.F, dropout, 0, 1234) if dropout > 0 else None
-    ref = cnn.forward_backward(DIMS, _as_oracle_params(DIMS, p), _bf16(x), labels, keep=keep, p=dropout,
-                               bf16_storage=True)
-    assert loss == pytest.approx(ref["loss"], rel=3e-2)
-    bad = []
-    for name, o, shape in cnn.layout(DIMS):
+    g = clf.grads().astype(np.float64)
+    keep = cnn.dropout_mask(dims.B, dims.F, dropout, 0, 1234) if dropout > 0 else None
+    q = _as_oracle_params(dims, p)
+    ref = cnn.forward_backward(dims, q, _bf16(x), labels, keep=keep, p=dropout, bf16_storage=True)
+    plain = cnn.forward_backward(dims, q, _bf16(x), labels, keep=keep, p=dropout, grads=False)
+    # every gradient entry
+    mag = ref["grad_mag"]
+    floor = np.empty_like(mag)
+    for name, o, shape in cnn.layout(dims):
         n = int(np.prod(shape))
-        a, b = g[o:o + n].astype(np.float64), ref["grads"][o:o + n]
-        if np.linalg.norm(b) < 1e-9:
-            if np.linalg.norm(a) >= 1e-6:
-                bad.append((name, "nonzero", float(np.linalg.norm(a))))
-            continue
-        cos = float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b)))
-        if not (_rel_l2(a, b) < 6e-2 and cos > 0.995):
-            bad.append((name, _rel_l2(a, b), cos))
-    assert not bad, bad
+        floor[o:o + n] = np.sqrt(np.mean(mag[o:o + n] ** 2))
+    bound = TAU * (mag + floor)
+    err = np.abs(g - ref["grads"])
+    worst = {}
+    for name, o, shape in cnn.layout(dims):
+        n = int(np.prod(shape))
+        worst[name] = float(np.max(err[o:o + n] / bound[o:o + n]))
+    if not (err <= bound).all():
+        bad = np.nonzero(err > bound)[0]
+        names = [next(nm for nm, o, sh in cnn.layout(dims) if o <= i < o + int(np.prod(sh))) for i in bad[:8]]
+        print("violations", len(bad), list(zip(names, g[bad[:8]], ref["grads"][bad[:8]], ref["grad_mag"][bad[:8]])))
+    assert (err <= bound).all(), sorted(worst.items(), key=lambda kv: -kv[1])[:4]
+    # the bound is not vacuous: the terms' magnitudes are within a factor of the gradients'
+    assert np.median(ref["grad_mag"] / np.maximum(np.abs(ref["grads"]), 1e-30)) < 200.0
+    # loss against both networks
+    k_loss = 2.0 ** -8 * abs(ref["loss"]) + 1e-6
+    assert abs(loss - ref["loss"]) <= k_loss
+    assert abs(loss - plain["loss"]) <= 3.0 * abs(ref["loss"] - plain["loss"]) + k_loss
     # running statistics: momentum 0.1 towards the batch mean / unbiased variance
     m, v = clf.bn_stats()
     np.testing.assert_allclose(m, 0.1 * ref["run_mean"], rtol=3e-2, atol=3e-3)
     np.testing.assert_allclose(v, 0.9 + 0.1 * ref["run_var"], rtol=3e-2, atol=3e-3)
     clf.close()
+    print(f"{dims.C} {dims.D}^3 dropout {dropout}: worst |err| / bound per tensor", worst)
 
 
-@pytest.mark.parametrize("dims", [DIMS, DIMS_HALO])
+@pytest.mark.parametrize("dims", [DIMS, DIMS_HALO, DIMS_PROD])
 def test_inference_matches_oracle_eval_mode(native, dims):
     DIMS = dims
     rng = np.random.default_rng(12)
@@ -121,9 +149,15 @@ def test_inference_matches_oracle_eval_mode(native, dims):
     clf.set_params(p)
     clf.set_bn_stats(rm, rv)
     z = clf.infer(torch.from_numpy(x).to(torch.bfloat16).cuda()).cpu().numpy()
-    ref = cnn.forward_backward(DIMS, _as_oracle_params(DIMS, p), _bf16(x), train=False, run_mean=rm,
-                               run_var=rv, grads=False, bf16_storage=True)
-    np.testing.assert_allclose(z, ref["logits"], rtol=3e-2, atol=3e-2)
+    q = _as_oracle_params(DIMS, p)
+    ref = cnn.forward_backward(DIMS, q, _bf16(x), train=False, run_mean=rm, run_var=rv, grads=False,
+                               bf16_storage=True)
+    plain = cnn.forward_backward(DIMS, q, _bf16(x), train=False, run_mean=rm, run_var=rv, grads=False)
+    # logits: within one BF16 unit of the storage network's (plus 1e-3 for FP32 sums over the head),
+    # and as close to the plain FP64 network as three times the storage rounding's effect
+    tol = 2.0 ** -7 * np.abs(ref["logits"]) + 1e-3
+    assert (np.abs(z - ref["logits"]) <= tol).all(), np.max(np.abs(z - ref["logits"]) / tol)
+    assert (np.abs(z - plain["logits"]) <= 3.0 * np.abs(ref["logits"] - plain["logits"]) + tol).all()
     clf.close()
 
 

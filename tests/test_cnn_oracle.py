@@ -180,3 +180,69 @@ def test_bf16_storage_mode_rounds_only_storage():
     assert b["loss"] != a["loss"]
     rounded = torch.tensor(b["logits"], dtype=torch.float32)
     assert torch.isfinite(rounded).all()
+
+
+def _torch_magnitudes(dims, params, x, labels, keep=None, p=0.0):
+    """Sum of the magnitudes of the terms of every gradient entry, from torch float64 autograd's
+    intermediate gradients: conv weights sum |dy| |a| over voxels (torch's conv3d weight gradient
+    of the absolute values), BN gamma / beta sum |dz yhat| / |dz| over voxels, the head's entries
+    sum over samples."""
+    P = torch.tensor(params, dtype=torch.float64, requires_grad=True)
+    t = {name: P[o:o + int(np.prod(shape))].reshape(shape) for name, o, shape in cnn.layout(dims)}
+    h = torch.tensor(x, dtype=torch.float64).permute(0, 4, 1, 2, 3)
+    keep_t = []
+    for l in range(4):
+        w = t[f"conv{l}.w"].permute(0, 4, 1, 2, 3)
+        a = h
+        y = F.conv3d(a, w, padding=1)
+        y.retain_grad()
+        mu = y.mean(dim=(0, 2, 3, 4), keepdim=True)
+        var = y.var(dim=(0, 2, 3, 4), unbiased=False, keepdim=True)
+        yhat = (y - mu) / torch.sqrt(var + 1e-5)
+        z = t[f"bn{l}.gamma"].view(1, -1, 1, 1, 1) * yhat + t[f"bn{l}.beta"].view(1, -1, 1, 1, 1)
+        z.retain_grad()
+        keep_t.append((a, w, y, yhat, z))
+        h = F.max_pool3d(F.relu(z), 2)
+    feat = h.permute(0, 2, 3, 4, 1).reshape(dims.B, -1)
+    pre = feat @ t["fc1.w"].T + t["fc1.b"]
+    pre.retain_grad()
+    h1 = F.relu(pre)
+    if keep is not None:
+        h1 = h1 * torch.tensor(keep, dtype=torch.float64) / (1.0 - p)
+    zl = h1 @ t["fc2.w"] + t["fc2.b"]
+    zl.retain_grad()
+    F.binary_cross_entropy_with_logits(zl, torch.tensor(labels, dtype=torch.float64)).backward()
+    mag = np.zeros_like(params)
+    lay = {name: (o, shape) for name, o, shape in cnn.layout(dims)}
+
+    def put(name, v):
+        o, shape = lay[name]
+        mag[o:o + int(np.prod(shape))] = v.detach().reshape(-1).numpy()
+
+    for l, (a, w, y, yhat, z) in enumerate(keep_t):
+        gw = torch.nn.grad.conv3d_weight(a.abs(), w.shape, y.grad.abs(), padding=1)   # [Co, Ci, kz, ky, kx]
+        put(f"conv{l}.w", gw.permute(0, 2, 3, 4, 1))
+        put(f"bn{l}.gamma", (z.grad * yhat).abs().sum(dim=(0, 2, 3, 4)))
+        put(f"bn{l}.beta", z.grad.abs().sum(dim=(0, 2, 3, 4)))
+    put("fc1.w", pre.grad.abs().T @ feat.abs())
+    put("fc1.b", pre.grad.abs().sum(dim=0))
+    put("fc2.w", zl.grad.abs() @ h1.abs())
+    put("fc2.b", zl.grad.abs().sum())
+    return mag
+
+
+@pytest.mark.parametrize("with_dropout", [False, True])
+def test_gradient_term_magnitudes_match_torch(with_dropout):
+    """The oracle's per-entry sum of term magnitudes (the scale of the GPU comparison's bound)
+    equals the one built from torch's intermediate gradients, and bounds |gradient|."""
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal((DIMS.B, DIMS.D, DIMS.H, DIMS.W, DIMS.C0))
+    labels = np.array([1.0, 0.0, 1.0])
+    params = _params(DIMS, 6)
+    keep = cnn.dropout_mask(DIMS.B, DIMS.F, 0.3, 1, 7) if with_dropout else None
+    p = 0.3 if with_dropout else 0.0
+    out = cnn.forward_backward(DIMS, params, x, labels, keep=keep, p=p)
+    ref = _torch_magnitudes(DIMS, params, x, labels, keep, p)
+    np.testing.assert_allclose(out["grad_mag"], ref, rtol=1e-9, atol=1e-12)
+    assert (out["grad_mag"] >= np.abs(out["grads"]) * (1 - 1e-12) - 1e-15).all()
+    assert (out["grad_mag"] > np.abs(out["grads"]) * 1.5).any()     # cancellations exist
