@@ -60,7 +60,8 @@ struct SearchParams {
     int32_t dtype;         // NSFRB_F32 / BF16 / F16
     int32_t n_sub, n_t;
     int32_t Tp;            // shared-memory row pitch (floats)
-    int32_t stage;         // 0 plain loads, 1 bulk FP32 direct, 2 bulk 16-bit staging
+    int32_t stage;         // 0 plain loads, 1 bulk FP32 direct, 2 bulk 16-bit staging (widened to
+                           // FP32), 3 bulk 16-bit direct (read in place by the barrier-free kernel)
     int32_t stg_pitch;     // staging row pitch in bytes (stage 2); fits any t_off % 8
     // ---- work items: item i -> pixel (pix_list ? pix_list[i] : pix0 + i)
     int64_t n_items;
@@ -85,7 +86,7 @@ struct SearchParams {
     int32_t gen_wi[kMaxW];
     int32_t n_dm;
     int32_t new_blk;       // > 0: only trials that end in the last new_blk samples
-    int32_t pipe;          // 1: barrier-free kernel (stage 1, KNOWN noise, candidates only)
+    int32_t pipe;          // 1: barrier-free kernel (stage 1 or 3, KNOWN noise, records only)
     // ---- outputs (indexed by absolute pixel)
     PixRec *rec;
     float *full_snr;       // [pix][n_dm][n_w] or nullptr
@@ -106,8 +107,9 @@ __host__ __device__ inline SmemLayout smem_layout(const SearchParams &p, int C) 
     L.table = o;
     o += align_up(sizeof(int32_t) * ((size_t)p.n_u * kInfo + p.n_deltas + (size_t)p.n_u * p.n_sub), 16);
     L.xs = o;
-    int nbuf = (p.stage == 1) ? 2 : 1;
-    o += align_up(sizeof(float) * (size_t)nbuf * p.n_sub * p.Tp, 128);
+    const int nbuf = (p.stage == 1 || p.stage == 3) ? 2 : 1;
+    const size_t es = (p.stage == 3) ? 2 : sizeof(float);
+    o += align_up(es * (size_t)nbuf * p.n_sub * p.Tp, 128);
     L.stg = o;
     if (p.stage == 2) o += align_up((size_t)2 * p.n_sub * p.stg_pitch, 128);
     L.pbuf = o;

@@ -105,10 +105,36 @@ void base_params(const nsfrb_plan_s *pl, SearchParams &sp) {
 }
 
 // Choose the staging scheme for a cube pointer / row geometry and size the
-// shared memory.  Returns false if nothing fits.
-bool choose_stage(const nsfrb_plan_s *pl, SearchParams &sp, size_t &smem) {
+// shared memory (chunk size C, the device's per-block limit).  Returns false if nothing fits.
+bool choose_stage_for(int C, int max_smem, SearchParams &sp, size_t &smem) {
     const uintptr_t base = reinterpret_cast<uintptr_t>(sp.cube);
     const int n_t = sp.n_t;
+    const int epv = 16 / static_cast<int>(elem_size(sp.dtype));   // samples per 16 bytes
+    // The barrier-free kernel: rows bulk-copied as stored (FP32, or 16-bit read in place, which
+    // needs the sample-pair path of even chunks), KNOWN noise, per-pixel records only.  The copy
+    // starts at the 16-byte boundary at or below the window start and must stay inside the row.
+    if (sp.t_wrap == 0 && sp.noise_mode == 0 && !sp.full_snr && (sp.dtype == NSFRB_F32 || C % 2 == 0) &&
+        base % 16 == 0 && sp.row_len % epv == 0) {
+        bool fits_row;
+        if (sp.t_off_dev)   // a ring row: the window start is below n_t, the row 2 n_t + 8 long
+            fits_row = sp.row_len >= 2 * static_cast<int64_t>(n_t) + 8;
+        else
+            fits_row = (sp.t_off - sp.t_off % epv) + static_cast<int64_t>(align_up(sp.t_off % epv + n_t, epv)) <=
+                       sp.row_len;
+        // odd chunks read one sample at a time without the tail mask: the copied window must be exact
+        const bool exact = !sp.t_off_dev && sp.t_off % epv == 0 && n_t % epv == 0;
+        if (fits_row && (C % 2 == 0 || exact)) {
+            sp.stage = (sp.dtype == NSFRB_F32) ? 1 : 3;
+            sp.stg_pitch = 0;
+            sp.pipe = 1;
+            const SmemLayout L = smem_layout(sp, C);
+            if (L.total <= static_cast<size_t>(max_smem)) {
+                smem = L.total;
+                return true;
+            }
+        }
+    }
+    sp.pipe = 0;
     int want = 0;
     if (sp.t_wrap > 0) {
         want = 0;   // ring rows: plain loads with the wrap-around index
@@ -125,17 +151,18 @@ bool choose_stage(const nsfrb_plan_s *pl, SearchParams &sp, size_t &smem) {
     for (int st = want; st >= 0; st = (st == 2 ? 0 : st - 1)) {
         sp.stage = st;
         sp.stg_pitch = (st == 2) ? static_cast<int32_t>(align_up(static_cast<size_t>(7 + n_t) * 2, 16)) : 0;
-        // the barrier-free kernel: FP32 rows copied straight in, KNOWN noise, records only
-        sp.pipe = (st == 1 && sp.noise_mode == 0 && !sp.full_snr && sp.new_blk == 0) ? 1 : 0;
-        if (sp.pipe && smem_layout(sp, pl->C).total > static_cast<size_t>(pl->max_smem)) sp.pipe = 0;
-        const SmemLayout L = smem_layout(sp, pl->C);
-        if (L.total <= static_cast<size_t>(pl->max_smem)) {
+        const SmemLayout L = smem_layout(sp, C);
+        if (L.total <= static_cast<size_t>(max_smem)) {
             smem = L.total;
             return true;
         }
         if (st == 0) break;
     }
     return false;
+}
+
+bool choose_stage(const nsfrb_plan_s *pl, SearchParams &sp, size_t &smem) {
+    return choose_stage_for(pl->C, pl->max_smem, sp, smem);
 }
 
 nsfrb_status ensure_device(nsfrb_plan_s *pl) {
@@ -372,7 +399,9 @@ nsfrb_status nsfrb_plan(const nsfrb_config *cfg, nsfrb_plan_t *out) {
     pl->C = pick_chunk(c.n_t);
     int smax_active = 0;
     for (int u = 0; u < pl->n_u_active; ++u) smax_active = std::max(smax_active, info[u * kInfo + UI_SMAX]);
-    pl->Tp = static_cast<int>(align_up(static_cast<size_t>(32 * pl->C + smax_active + 1), 4));
+    // a row holds the window from element eoff < 8 (a window start below a 16-byte boundary) up to
+    // the last sample a lane chunk reads, 32 C + smax - 1, and one more
+    pl->Tp = static_cast<int>(align_up(static_cast<size_t>(32 * pl->C + smax_active + 1 + 7), 8));
     for (int i = 0; i < c.n_w; ++i) {
         const int w = pl->widths[i];
         pl->wclass[i] = WC_GENERIC;

@@ -80,6 +80,7 @@ size_t elem_size(int dtype);
 void destroy_stream_state(nsfrb_plan_s *pl);
 void base_params(const nsfrb_plan_s *pl, SearchParams &sp);
 bool choose_stage(const nsfrb_plan_s *pl, SearchParams &sp, size_t &smem);
+bool choose_stage_for(int C, int max_smem, SearchParams &sp, size_t &smem);
 
 cudaError_t launch_search_c1(const SearchParams &, int, size_t, cudaStream_t);
 cudaError_t launch_search_c3(const SearchParams &, int, size_t, cudaStream_t);

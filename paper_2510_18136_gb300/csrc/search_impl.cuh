@@ -352,30 +352,89 @@ __device__ __forceinline__ void acc_pairs(float2 (&D)[C / 2], const float *xr, b
     }
 }
 
+// 16-bit storage read in place: x + y and y - x with x a BF16 (ST = 1) or FP16 (ST = 2) value and
+// y FP32, by the mixed-precision add and fma of sm_100+.  x widens exactly, so each result is the
+// FP32 operation on the widened value, rounded once: the same values as widening first.
+template <int ST>
+__device__ __forceinline__ float2 add16x2(float2 d, uint32_t u) {
+    float2 r;
+    if constexpr (ST == 1)
+        asm("{\n\t.reg .b16 l, h;\n\tmov.b32 {l, h}, %2;\n\tadd.rn.f32.bf16 %0, l, %3;\n\t"
+            "add.rn.f32.bf16 %1, h, %4;\n\t}"
+            : "=f"(r.x), "=f"(r.y) : "r"(u), "f"(d.x), "f"(d.y));
+    else
+        asm("{\n\t.reg .b16 l, h;\n\tmov.b32 {l, h}, %2;\n\tadd.rn.f32.f16 %0, l, %3;\n\t"
+            "add.rn.f32.f16 %1, h, %4;\n\t}"
+            : "=f"(r.x), "=f"(r.y) : "r"(u), "f"(d.x), "f"(d.y));
+    return r;
+}
+// d - x = fma(x, -1, d): the product is exact, the one rounding that of the subtraction.
+template <int ST>
+__device__ __forceinline__ float2 sub16x2(float2 d, uint32_t u) {
+    float2 r;
+    if constexpr (ST == 1)
+        asm("{\n\t.reg .b16 l, h, m;\n\tmov.b32 {l, h}, %2;\n\tmov.b16 m, 0xBF80;\n\t"
+            "fma.rn.f32.bf16 %0, l, m, %3;\n\tfma.rn.f32.bf16 %1, h, m, %4;\n\t}"
+            : "=f"(r.x), "=f"(r.y) : "r"(u), "f"(d.x), "f"(d.y));
+    else
+        asm("{\n\t.reg .b16 l, h, m;\n\tmov.b32 {l, h}, %2;\n\tmov.b16 m, 0xBC00;\n\t"
+            "fma.rn.f32.f16 %0, l, m, %3;\n\tfma.rn.f32.f16 %1, h, m, %4;\n\t}"
+            : "=f"(r.x), "=f"(r.y) : "r"(u), "f"(d.x), "f"(d.y));
+    return r;
+}
+
+// D[c] += x[e + c] (SUB: D[c] -= x[e + c]) for c < C from a 16-bit row in shared memory read as
+// 32-bit words (two samples each); for odd e the pair (x[e + 2m], x[e + 2m + 1]) straddles two
+// words and is reassembled by a byte permute.
+template <int C, bool SUB, int ST>
+__device__ __forceinline__ void acc_pairs16(float2 (&D)[C / 2], const uint16_t *row, int e) {
+    const uint32_t *w = reinterpret_cast<const uint32_t *>(row + (e & ~1));
+    if (!(e & 1)) {
+#pragma unroll
+        for (int m = 0; m < C / 2; ++m) D[m] = SUB ? sub16x2<ST>(D[m], w[m]) : add16x2<ST>(D[m], w[m]);
+    } else {
+        uint32_t lo = w[0];
+#pragma unroll
+        for (int m = 0; m < C / 2; ++m) {
+            const uint32_t hi = w[m + 1];
+            const uint32_t u = __byte_perm(lo, hi, 0x5432);
+            D[m] = SUB ? sub16x2<ST>(D[m], u) : add16x2<ST>(D[m], u);
+            lo = hi;
+        }
+    }
+}
+
+// Subband row k of a pixel tile in storage ST, its sample t + s (window offset eoff within the row).
+template <int C, bool SUB, int ST>
+__device__ __forceinline__ void acc_row(float2 (&D)[C / 2], const void *xs, int Tp, int k, int e) {
+    if constexpr (ST == 0) {
+        const float *r = static_cast<const float *>(xs) + (size_t)k * Tp + e;
+        acc_pairs<C, SUB>(D, r, e & 1);
+    } else {
+        acc_pairs16<C, SUB, ST>(D, static_cast<const uint16_t *>(xs) + (size_t)k * Tp, e);
+    }
+}
+
 // First row of a group: D = sum over subbands k of x_k(t + s_k), subbands in order.
-template <int C>
-__device__ __forceinline__ void dd_first(float2 (&D)[C / 2], const float *xs, int Tp, int n_sub,
+template <int C, int ST>
+__device__ __forceinline__ void dd_first(float2 (&D)[C / 2], const void *xs, int Tp, int n_sub,
                                          const int32_t *sh, int t0) {
 #pragma unroll
     for (int m = 0; m < C / 2; ++m) D[m] = make_float2(0.0f, 0.0f);
 #pragma unroll 1
-    for (int k = 0; k < n_sub; ++k) {
-        const int s = sh[k];
-        acc_pairs<C, false>(D, xs + (size_t)k * Tp + t0 + s, s & 1);
-    }
+    for (int k = 0; k < n_sub; ++k) acc_row<C, false, ST>(D, xs, Tp, k, t0 + sh[k]);
 }
 
 // Next row from the previous one: per changed subband, D = (D + x_k(t + s_new)) - x_k(t + s_old).
-template <int C>
-__device__ __forceinline__ void dd_delta(float2 (&D)[C / 2], const float *xs, int Tp, const int32_t *s_delta,
+template <int C, int ST>
+__device__ __forceinline__ void dd_delta(float2 (&D)[C / 2], const void *xs, int Tp, const int32_t *s_delta,
                                          int d0, int nd, int t0) {
 #pragma unroll 1
     for (int e = d0; e < d0 + nd; ++e) {
         const uint32_t pk = static_cast<uint32_t>(s_delta[e]);
         const int k = pk & 63u, so = (pk >> 6) & 0x1fffu, sn = pk >> 19;
-        const float *row = xs + (size_t)k * Tp + t0;
-        acc_pairs<C, false>(D, row + sn, sn & 1);
-        acc_pairs<C, true>(D, row + so, so & 1);
+        acc_row<C, false, ST>(D, xs, Tp, k, t0 + sn);
+        acc_row<C, true, ST>(D, xs, Tp, k, t0 + so);
     }
 }
 
@@ -742,16 +801,20 @@ __device__ __forceinline__ int find_t_even(const SearchParams &p, const float2 (
     return warp_min(t);
 }
 
-// search_rows for even chunks (sample pairs, see above).
-template <int C, bool FULL>
-__device__ __forceinline__ PixRec search_rows_even(const SearchParams &p, const float *xs, float *Pw,
+// search_rows for even chunks (sample pairs, see above).  The pixel's rows are in storage ST
+// (0 FP32, 1 BF16, 2 FP16) with the window at element eoff of each row; with mask_tail the
+// elements past the window are not -inf and the de-dispersed samples past L are set to -inf.
+template <int C, bool FULL, int ST = 0>
+__device__ __forceinline__ PixRec search_rows_even(const SearchParams &p, const void *xs, float *Pw,
                                                    const float *s_inv, const int32_t *s_info,
                                                    const int32_t *s_delta, const int32_t *s_shift, int u_lo,
-                                                   int u_hi, int64_t pix, int lane) {
+                                                   int u_hi, int64_t pix, int lane, int eoff = 0,
+                                                   bool mask_tail = false) {
     static_assert(C % 2 == 0, "even chunks only");
     constexpr int SH = (C < kSmallMax) ? C : kSmallMax;
     const int n_sub = p.n_sub, n_t = p.n_t, Tp = p.Tp;
     const int t0 = lane * C;
+    const int te = t0 + eoff;
     const bool masked = p.new_blk > 0;
     float bsnr = neg_inf();
     int bu = -1, bwi = -1, bt = -1;
@@ -760,10 +823,17 @@ __device__ __forceinline__ PixRec search_rows_even(const SearchParams &p, const 
     for (int u = u_lo; u < u_hi; ++u) {
         const int32_t *info = s_info + u * kInfo;
         if (u == u_lo)
-            dd_first<C>(D, xs, Tp, n_sub, s_shift + u * n_sub, t0);
+            dd_first<C, ST>(D, xs, Tp, n_sub, s_shift + u * n_sub, te);
         else
-            dd_delta<C>(D, xs, Tp, s_delta, info[UI_DOFF], info[UI_ND], t0);
+            dd_delta<C, ST>(D, xs, Tp, s_delta, info[UI_DOFF], info[UI_ND], te);
         const int L = n_t - info[UI_SMAX];
+        if (mask_tail) {
+#pragma unroll
+            for (int m = 0; m < C / 2; ++m) {
+                if (t0 + 2 * m >= L) D[m].x = neg_inf();
+                if (t0 + 2 * m + 1 >= L) D[m].y = neg_inf();
+            }
+        }
 
         float ls = neg_inf();
         int lw = -1;
@@ -879,16 +949,20 @@ __device__ __forceinline__ PixRec search_rows_even(const SearchParams &p, const 
     return PixRec{bsnr, bu, bwi, bt};
 }
 
-// Per-warp row search for chunk size C (pairs for even C).
-template <int C, bool FULL>
-__device__ __forceinline__ PixRec search_rows_any(const SearchParams &p, const float *xs, float *Pw, const float *s_inv,
+// Per-warp row search for chunk size C (pairs for even C).  Odd chunks read FP32 rows only.
+template <int C, bool FULL, int ST = 0>
+__device__ __forceinline__ PixRec search_rows_any(const SearchParams &p, const void *xs, float *Pw, const float *s_inv,
                                                   const int32_t *s_info, const int32_t *s_delta,
                                                   const int32_t *s_shift, int u_lo, int u_hi, int64_t pix,
-                                                  int lane) {
-    if constexpr (C % 2 == 0)
-        return search_rows_even<C, FULL>(p, xs, Pw, s_inv, s_info, s_delta, s_shift, u_lo, u_hi, pix, lane);
-    else
-        return search_rows<C, FULL>(p, xs, Pw, s_inv, s_info, s_delta, s_shift, u_lo, u_hi, pix, lane);
+                                                  int lane, int eoff = 0, bool mask_tail = false) {
+    if constexpr (C % 2 == 0) {
+        return search_rows_even<C, FULL, ST>(p, xs, Pw, s_inv, s_info, s_delta, s_shift, u_lo, u_hi, pix, lane,
+                                             eoff, mask_tail);
+    } else {
+        static_assert(ST == 0, "odd chunks read FP32 rows");
+        return search_rows<C, FULL>(p, static_cast<const float *>(xs) + eoff, Pw, s_inv, s_info, s_delta, s_shift,
+                                    u_lo, u_hi, pix, lane);
+    }
 }
 
 // ------------------------------------------------------------------ the kernel
@@ -1088,7 +1162,7 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel(const __grid_consta
         // ---- per-warp search over its rows
         PixRec wr{neg_inf(), -1, -1, -1};
         if (!bad_pixel)
-            wr = search_rows_any<C, FULL>(p, xs, Pw, s_inv, s_info, s_delta, s_shift, u_lo, u_hi, pix, lane);
+            wr = search_rows_any<C, FULL, 0>(p, xs, Pw, s_inv, s_info, s_delta, s_shift, u_lo, u_hi, pix, lane);
         const float bsnr = wr.snr;
         const int bu = wr.dm_idx, bwi = wr.w_idx, bt = wr.t_idx;
         // FULL mode: DM rows that have no trial at all
@@ -1126,19 +1200,26 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel(const __grid_consta
 
 // ------------------------------------------------------------------ barrier-free kernel
 
-// Same search (FP32 rows bulk-copied straight into a double buffer, KNOWN noise, per-pixel
-// records only) without CTA barriers between pixels.  Every warp walks the CTA's pixels on
-// its own; on the CTA's i-th pixel warp w takes row group (w + i) mod kWarps, so the groups
-// with one row more rotate over the warps.  A warp publishes its group's best and counts
-// itself done; the last warp of a pixel combines the groups in row order (the DM tie rule),
-// writes the pixel's record, and starts the copy of the pixel two ahead into the buffer it
-// frees (with that pixel's 1 / (sigma sqrt(w))).  Warps drift apart by at most one pixel.
-template <int C>
+// Same search (rows bulk-copied straight into a double buffer, KNOWN noise, per-pixel records only)
+// without CTA barriers between pixels.  Every warp walks the CTA's pixels on its own; on the CTA's
+// i-th pixel warp w takes row group (w + i) mod kWarps, so the groups with one row more rotate over
+// the warps.  A warp publishes its group's best and counts itself done; the last warp of a pixel
+// combines the groups in row order (the DM tie rule), writes the pixel's record, and starts the copy
+// of the pixel two ahead into the buffer it frees (with that pixel's 1 / (sigma sqrt(w))).  Warps
+// drift apart by at most one pixel.
+// ST is the storage type of the rows, kept as they are in shared memory: FP32, or BF16 / FP16 read
+// in place by the mixed-precision adds (no widening pass).  A window that starts at any sample t_off
+// is copied from the 16-byte boundary below it and read from element eoff = t_off mod (16 / size)
+// of the staged row; when the copy then carries samples past the window, the de-dispersed samples
+// past the valid range are set to -inf instead of relying on -inf past the window.
+template <int C, int ST>
 __global__ void __launch_bounds__(kThreads, 1) search_kernel_pipe(const __grid_constant__ SearchParams p) {
     extern __shared__ __align__(128) unsigned char smem[];
+    constexpr int kEs = (ST == 0) ? 4 : 2;          // bytes per stored sample
+    constexpr int kEpv = 16 / kEs;                  // samples per 16 bytes
     const SmemLayout lay = smem_layout(p, C);
     int32_t *s_table = reinterpret_cast<int32_t *>(smem + lay.table);
-    float *s_xs = reinterpret_cast<float *>(smem + lay.xs);
+    unsigned char *s_xs = smem + lay.xs;
     float *s_pbuf = reinterpret_cast<float *>(smem + lay.pbuf);
     PixRec *s_wbest = reinterpret_cast<PixRec *>(smem + lay.wbest);        // [2][kWarps] by row group
     float *s_inv = reinterpret_cast<float *>(smem + lay.sinv);             // [2][kMaxW]
@@ -1150,16 +1231,25 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel_pipe(const __grid_c
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n_sub = p.n_sub, n_t = p.n_t, Tp = p.Tp;
     const int t_off = p.t_off_dev ? *p.t_off_dev : p.t_off;
+    const int eoff = t_off & (kEpv - 1);
+    const int row_elems = static_cast<int>(align_up(static_cast<size_t>(eoff + n_t), kEpv));
+    const bool mask_tail = row_elems != eoff + n_t;
+    const size_t buf_bytes = (size_t)n_sub * Tp * kEs;
 
     const int table_words = p.n_u * kInfo + p.n_deltas + p.n_u * n_sub;
     for (int i = tid; i < table_words; i += kThreads) s_table[i] = p.table[i];
     const int32_t *s_info = s_table;
     const int32_t *s_delta = s_table + p.n_u * kInfo;
     const int32_t *s_shift = s_delta + p.n_deltas;
+    // -inf past the copied part of every row of both buffers (never overwritten)
     for (int b = 0; b < 2; ++b)
-        for (int i = tid; i < n_sub * (Tp - n_t); i += kThreads) {
-            const int k = i / (Tp - n_t), t = n_t + i % (Tp - n_t);
-            s_xs[(size_t)b * n_sub * Tp + (size_t)k * Tp + t] = neg_inf();
+        for (int i = tid; i < n_sub * (Tp - row_elems); i += kThreads) {
+            const int k = i / (Tp - row_elems), t = row_elems + i % (Tp - row_elems);
+            unsigned char *row = s_xs + b * buf_bytes + (size_t)k * Tp * kEs;
+            if constexpr (ST == 0)
+                reinterpret_cast<float *>(row)[t] = neg_inf();
+            else
+                reinterpret_cast<uint16_t *>(row)[t] = (ST == 1) ? 0xFF80u : 0xFC00u;
         }
 
     int64_t n_items = p.n_items;
@@ -1176,13 +1266,14 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel_pipe(const __grid_c
             s_inv[b * kMaxW + lane] = 1.0f / (sg * sqrtf(static_cast<float>(p.widths[lane])));
         }
         __syncwarp();
-        if (lane == 0) mbar_expect_tx(&s_bar[b], static_cast<uint32_t>(n_sub * n_t * 4));
+        const uint32_t bytes = static_cast<uint32_t>(row_elems * kEs);
+        if (lane == 0) mbar_expect_tx(&s_bar[b], bytes * static_cast<uint32_t>(n_sub));
         __syncwarp();
-        const float *src = static_cast<const float *>(p.cube);
+        const unsigned char *src = static_cast<const unsigned char *>(p.cube);
         const int64_t row0 = (pix - p.cube_pix0) * n_sub;
-        float *dst = s_xs + (size_t)b * n_sub * Tp;
+        unsigned char *dst = s_xs + b * buf_bytes;
         for (int k = lane; k < n_sub; k += 32)
-            bulk_g2s(dst + (size_t)k * Tp, src + (row0 + k) * p.row_len + t_off, static_cast<uint32_t>(n_t * 4),
+            bulk_g2s(dst + (size_t)k * Tp * kEs, src + ((row0 + k) * p.row_len + t_off - eoff) * kEs, bytes,
                      &s_bar[b]);
     };
     if (tid == 0) {
@@ -1217,8 +1308,8 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel_pipe(const __grid_c
         const int g = (warp + i) % kWarps;
         const int u_lo = (g * n_ua) / kWarps, u_hi = ((g + 1) * n_ua) / kWarps;
         const int64_t pix = item_pixel(it);
-        const PixRec wr = search_rows_any<C, false>(p, s_xs + (size_t)b * n_sub * Tp, Pw, s_inv + b * kMaxW,
-                                                    s_info, s_delta, s_shift, u_lo, u_hi, pix, lane);
+        const PixRec wr = search_rows_any<C, false, ST>(p, s_xs + b * buf_bytes, Pw, s_inv + b * kMaxW, s_info,
+                                                        s_delta, s_shift, u_lo, u_hi, pix, lane, eoff, mask_tail);
         // publish; this warp's reads of buffer b are done before the copy that refills it
         fence_proxy_async();
         int last = 0;
@@ -1256,25 +1347,49 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel_pipe(const __grid_c
 
 }  // namespace dev
 
+// 16-bit rows read in place need the sample-pair path (even chunks); odd chunks get FP32 only.
+#define NSFRB_PIPE_LAUNCH(CC, ST)                                                              \
+    dev::search_kernel_pipe<CC, ST><<<grid, kThreads, smem, s>>>(p)
 #define NSFRB_INSTANTIATE_SEARCH(CC)                                                           \
     cudaError_t launch_search_c##CC(const SearchParams &p, int grid, size_t smem, cudaStream_t s) { \
-        if (p.pipe)                                                                            \
-            dev::search_kernel_pipe<CC><<<grid, kThreads, smem, s>>>(p);                       \
-        else if (p.full_snr)                                                                   \
+        if (p.pipe) {                                                                          \
+            if constexpr (CC % 2 == 0) {                                                       \
+                if (p.dtype == 1)                                                              \
+                    NSFRB_PIPE_LAUNCH(CC, 1);                                                  \
+                else if (p.dtype == 2)                                                         \
+                    NSFRB_PIPE_LAUNCH(CC, 2);                                                  \
+                else                                                                           \
+                    NSFRB_PIPE_LAUNCH(CC, 0);                                                  \
+            } else {                                                                           \
+                if (p.dtype != 0) return cudaErrorInvalidValue;                                \
+                NSFRB_PIPE_LAUNCH(CC, 0);                                                      \
+            }                                                                                  \
+        } else if (p.full_snr) {                                                               \
             dev::search_kernel<CC, true><<<grid, kThreads, smem, s>>>(p);                      \
-        else                                                                                   \
+        } else {                                                                               \
             dev::search_kernel<CC, false><<<grid, kThreads, smem, s>>>(p);                     \
+        }                                                                                      \
         return cudaGetLastError();                                                             \
     }                                                                                          \
     cudaError_t prepare_search_c##CC(size_t smem) {                                            \
+        const int sm = static_cast<int>(smem);                                                 \
         cudaError_t e = cudaFuncSetAttribute(dev::search_kernel<CC, false>,                    \
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-        if (e != cudaSuccess) return e;                                                        \
-        e = cudaFuncSetAttribute(dev::search_kernel_pipe<CC>,                                  \
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);      \
-        if (e != cudaSuccess) return e;                                                        \
-        return cudaFuncSetAttribute(dev::search_kernel<CC, true>,                              \
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);   \
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, sm); \
+        if (e == cudaSuccess)                                                                  \
+            e = cudaFuncSetAttribute(dev::search_kernel<CC, true>,                             \
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, sm);         \
+        if (e == cudaSuccess)                                                                  \
+            e = cudaFuncSetAttribute(dev::search_kernel_pipe<CC, 0>,                           \
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, sm);         \
+        if constexpr (CC % 2 == 0) {                                                           \
+            if (e == cudaSuccess)                                                              \
+                e = cudaFuncSetAttribute(dev::search_kernel_pipe<CC, 1>,                       \
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, sm);     \
+            if (e == cudaSuccess)                                                              \
+                e = cudaFuncSetAttribute(dev::search_kernel_pipe<CC, 2>,                       \
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, sm);     \
+        }                                                                                      \
+        return e;                                                                              \
     }
 
 }  // namespace nsfrb

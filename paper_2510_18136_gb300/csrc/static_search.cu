@@ -75,29 +75,11 @@ __global__ void __launch_bounds__(kCompactBlock) static_scatter_kernel(const Pix
     }
 }
 
-// Staging scheme for a contiguous cube under this device's shared-memory limit:
-// bulk copies when the rows are 16-byte aligned, plain loads otherwise.  FP32 cubes with
-// known noise take the barrier-free kernel, as nsfrb_search does, when its layout fits.
-bool static_stage(int C, int max_smem, SearchParams &sp, size_t &smem) {
-    const uintptr_t base = reinterpret_cast<uintptr_t>(sp.cube);
-    int want = 0;
-    if (sp.dtype == NSFRB_F32)
-        want = (base % 16 == 0 && sp.n_t % 4 == 0) ? 1 : 0;
-    else
-        want = (base % 16 == 0 && sp.n_t % 8 == 0) ? 2 : 0;
-    for (int st : {want, 0}) {
-        sp.stage = st;
-        sp.stg_pitch = (st == 2) ? static_cast<int32_t>(align_up(static_cast<size_t>(7 + sp.n_t) * 2, 16)) : 0;
-        sp.pipe = (st == 1 && sp.noise_mode == 0 && !sp.full_snr && sp.new_blk == 0) ? 1 : 0;
-        if (sp.pipe && smem_layout(sp, C).total > static_cast<size_t>(max_smem)) sp.pipe = 0;
-        const SmemLayout L = smem_layout(sp, C);
-        if (L.total <= static_cast<size_t>(max_smem)) {
-            smem = L.total;
-            return true;
-        }
-    }
-    return false;
-}
+// Staging scheme for a contiguous cube under this device's shared-memory limit, as nsfrb_search
+// chooses it: the barrier-free kernel for cubes with known noise whose rows are 16-byte aligned
+// (FP32 rows copied as they are, 16-bit rows read in place), else bulk copies with per-pixel
+// barriers, else plain loads.
+bool static_stage(int C, int max_smem, SearchParams &sp, size_t &smem) { return choose_stage_for(C, max_smem, sp, smem); }
 
 // Once per device, with that device current: the device address of the
 // scratch array (its host-side name is only a stand-in) and the kernel's

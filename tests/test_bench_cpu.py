@@ -32,7 +32,9 @@ def test_reference_arm_prints_one_json_line():
 def test_search_kernel_name_follows_the_chunk_rule():
     sys.path.insert(0, ROOT)
     import bench
-    assert bench.search_kernel_name(1200, "f32") == "search_kernel_pipe<38>"
-    assert bench.search_kernel_name(1200, "bf16") == "search_kernel<38, false>"
-    assert bench.search_kernel_name(1247, "f32") == "search_kernel_pipe<39>"
-    assert bench.search_kernel_name(64, "f32") == "search_kernel_pipe<3>"
+    assert bench.search_kernel_name(1200, "f32") == "search_kernel_pipe<38, 0>"
+    assert bench.search_kernel_name(1200, "bf16") == "search_kernel_pipe<38, 1>"
+    assert bench.search_kernel_name(1200, "bf16", "mad") == "search_kernel<38, false>"
+    assert bench.search_kernel_name(1247, "f32") == "search_kernel_pipe<39, 0>"
+    assert bench.search_kernel_name(64, "f32") == "search_kernel_pipe<3, 0>"
+    assert bench.search_kernel_name(1001, "bf16") == "search_kernel<38, false>"

@@ -227,3 +227,25 @@ def test_candidate_capacity_truncation(native):
     with pytest.raises(native.NsfrbError) as e:
         plan.candidates(cap=5)
     assert e.value.status == native.ETRUNC
+
+
+# ----------------------------------------------------------------------------- records mode (barrier-free kernel)
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "f16"])
+@pytest.mark.parametrize("n_t", [801, 1000, 1001, 1200, 1215])
+def test_records_mode_parity(native, dtype, n_t):
+    """Per-pixel records and candidates without FULL arrays: the barrier-free kernel for FP32 rows
+    and for 16-bit rows read in place (even chunks; window lengths that are not a multiple of the
+    16-byte sample count take the staged kernel), against the FP64 oracle on the stored values."""
+    rng = np.random.default_rng(n_t + len(dtype))
+    widths = [1, 2, 3, 4, 8, 16, 32, 64, 96, 128, 256, 512, 800]
+    cfg = synth.SearchConfig(ny=5, nx=9, n_t=n_t, dm=np.sort(rng.uniform(0, 2500, 37)),
+                             widths=np.array(widths, np.int32), threshold=4.5)
+    tdt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[dtype]
+    cube = _psf_cube(cfg, n_t, 5, dm_range=(0.0, 2500.0)).to(tdt)
+    sig = rng.uniform(4.0, 8.0, cfg.n_pix).astype(np.float32)
+    cand, snr, idx, _ = _run(native, cfg, cube, sig, dtype=dtype, out="candidates")
+    tab, res, best, bad = _oracle(cfg, cube.float().numpy(), sigma=sig)
+    parity.compare_best(snr, idx, best)
+    parity.compare_candidates(cand, best, cfg.threshold, np.arange(cfg.n_pix), cfg.nx)
+    assert len(cand) > 0

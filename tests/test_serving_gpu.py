@@ -170,3 +170,40 @@ def test_stream_bf16_rescore_from_fp32_window(native, n_blk):
                     assert abs(got[p] - s16) <= parity.tol(s16)
     assert n_rescored > 0
     plan.close()
+
+
+@pytest.mark.parametrize("dtype,n_blk", [("f32", 25), ("bf16", 25), ("f16", 12), ("bf16", 7)])
+def test_stream_long_window(native, dtype, n_blk):
+    """A window of 832 samples (the sample-pair chunk): the window start moves by n_blk per block,
+    so the barrier-free kernel reads every row from an offset below a 16-byte boundary and sets the
+    de-dispersed samples past the valid range to -inf."""
+    cfg = synth.SearchConfig(ny=3, nx=5, n_t=832, dm=np.linspace(0, 1500, 24),
+                             widths=np.array([1, 2, 4, 8, 16, 32, 64, 100, 128, 256], np.int32), threshold=5.0)
+    n_blocks = max(6, 160 // n_blk)
+    start = (cfg.n_t // n_blk - 2) * n_blk       # check from a nearly full window on
+    total = start + n_blk * n_blocks
+    x = _series(cfg, total, 13, n_inj=6)
+    if dtype != "f32":
+        tdt = torch.bfloat16 if dtype == "bf16" else torch.float16
+        x = x.to(tdt).to(torch.float32)
+    xn = x.numpy()
+    tab = oracle.delay_table(cfg.freq_mhz, cfg.dm)
+    plan = native.Plan(cfg, dtype=dtype)
+    plan.stream_open(n_blk)
+    pushed = 0
+    n_cand = 0
+    while pushed < total:
+        nb = n_blk
+        blk = torch.from_numpy(xn[:, :, pushed:pushed + nb].transpose(2, 1, 0).copy())
+        plan.stream_push(blk.reshape(nb, cfg.n_sub, cfg.ny, cfg.nx).contiguous())
+        cand, _ = plan.stream_poll(timeout_ms=10000)
+        pushed += nb
+        if pushed >= start:
+            lo = max(0, pushed - cfg.n_t)
+            window = np.zeros((cfg.n_pix, cfg.n_sub, cfg.n_t), np.float32)
+            window[:, :, cfg.n_t - (pushed - lo):] = xn[:, :, lo:pushed]
+            best = _window_oracle(cfg, window, n_blk, tab)
+            parity.compare_candidates(cand, best, cfg.threshold, np.arange(cfg.n_pix), cfg.nx)
+            n_cand += len(cand)
+    assert n_cand > 0
+    plan.close()
