@@ -92,6 +92,8 @@ struct SearchParams {
     float *full_snr;       // [pix][n_dm][n_w] or nullptr
     int16_t *full_t;
     int32_t *err;
+    const uint8_t *bad_pix;   // barrier-free kernel: pixels flagged here (by absolute index) get an
+                              // invalid record (S/N -inf) and ERR_ZERO_MAD (normalised slabs)
 };
 
 // Shared-memory carve-up, identical on host and device.
@@ -153,5 +155,11 @@ cudaError_t launch_compact(const PixRec *rec, int64_t n_pix, int32_t nx, float t
 cudaError_t launch_rescore_select(const PixRec *rec, int64_t n_pix, float thr, float eps,
                                   int32_t *list, int32_t *n_list, cudaStream_t s);
 constexpr int kCompactBlock = 1024;
+
+// Median / MAD normalisation of pixels [pix0, pix0 + n_pix) of a pixel-major cube ([pix][sub][n_t],
+// rows of n_t samples in `dtype`) into out ([n_pix][n_sub][n_t] FP32); bad[pixel] = 1 where a row
+// has zero MAD (bad must be cleared by the caller).
+cudaError_t launch_mad_normalise(const void *cube, int dtype, int64_t pix0, int64_t n_pix, int n_sub, int n_t,
+                                 float *out, uint8_t *bad, int n_sm, cudaStream_t s);
 
 }  // namespace nsfrb

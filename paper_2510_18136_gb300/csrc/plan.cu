@@ -247,6 +247,58 @@ nsfrb_status queue_search(nsfrb_plan_s *pl, const void *cube, int64_t cube_pix0,
     return cuda_check(pl, launch_search(pl->C, sp, grid, smem, s), "search launch");
 }
 
+// MAD mode with per-pixel records: the median / MAD normalisation as a pass of its own, slab by
+// slab of pixels into an FP32 workspace, each slab then searched by the barrier-free kernel with
+// unit noise per sample (sigma_D = sqrt(n_sub)); pixels with a zero-MAD row get invalid records.
+// Returns false (nothing queued) where this does not apply: FULL output, or windows whose FP32
+// rows do not fill whole 16-byte units.
+bool mad_slabs_apply(const nsfrb_plan_s *pl) {
+    const nsfrb_config &c = pl->cfg;
+    return c.noise_mode == NSFRB_NOISE_MAD && c.out_mode == NSFRB_OUT_CANDIDATES && c.n_t % 4 == 0;
+}
+
+nsfrb_status queue_search_mad(nsfrb_plan_s *pl, const void *cube, int dtype, int64_t pix0, int64_t n,
+                              cudaStream_t s) {
+    const nsfrb_config &c = pl->cfg;
+    const int64_t n_pix = static_cast<int64_t>(c.ny) * c.nx;
+    nsfrb_status st;
+    if (!pl->d_madws) {
+        const size_t pix_bytes = sizeof(float) * static_cast<size_t>(c.n_sub) * c.n_t;
+        pl->mad_slab = std::min<int64_t>(n_pix, std::max<int64_t>(1, (int64_t(2) << 30) / static_cast<int64_t>(pix_bytes)));
+        if (cudaMalloc(reinterpret_cast<void **>(&pl->d_madws), pix_bytes * pl->mad_slab) != cudaSuccess ||
+            cudaMalloc(reinterpret_cast<void **>(&pl->d_bad), static_cast<size_t>(n_pix)) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(pl->d_madws);
+            pl->d_madws = nullptr;
+            return fail(pl, NSFRB_ENOMEM, "cudaMalloc MAD normalisation workspace");
+        }
+    }
+    if ((st = cuda_check(pl, cudaMemsetAsync(pl->d_bad + pix0, 0, static_cast<size_t>(n), s), "memset"))) return st;
+    for (int64_t p0 = pix0; p0 < pix0 + n; p0 += pl->mad_slab) {
+        const int64_t m = std::min<int64_t>(pl->mad_slab, pix0 + n - p0);
+        if ((st = cuda_check(pl,
+                             launch_mad_normalise(cube, dtype, p0, m, c.n_sub, c.n_t, pl->d_madws, pl->d_bad,
+                                                  pl->n_sm, s),
+                             "MAD normalisation")) != NSFRB_OK)
+            return st;
+        SearchParams sp;
+        base_params(pl, sp);
+        sp.noise_mode = NSFRB_NOISE_KNOWN;   // the slab holds normalised samples of unit noise
+        sp.bad_pix = pl->d_bad;
+        sp.cube = pl->d_madws;
+        sp.cube_pix0 = p0;
+        sp.dtype = NSFRB_F32;
+        sp.row_len = c.n_t;
+        sp.pix0 = p0;
+        sp.n_items = m;
+        size_t smem = 0;
+        if (!choose_stage(pl, sp, smem)) return fail(pl, NSFRB_EINVAL, "shared memory does not fit this plan");
+        const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(m, pl->n_sm)));
+        if ((st = cuda_check(pl, launch_search(pl->C, sp, grid, smem, s), "search launch")) != NSFRB_OK) return st;
+    }
+    return NSFRB_OK;
+}
+
 nsfrb_status queue_finish(nsfrb_plan_s *pl, cudaStream_t s) {
     const nsfrb_config &c = pl->cfg;
     const int64_t n_pix = static_cast<int64_t>(c.ny) * c.nx;
@@ -454,9 +506,11 @@ nsfrb_status nsfrb_search(nsfrb_plan_t plan, const void *d_cube, const float *d_
     if ((st = cuda_check(plan, cudaMemsetAsync(plan->d_err, 0, sizeof(int32_t), s), "memset")) != NSFRB_OK)
         return st;
     if ((st = cuda_check(plan, cudaEventRecord(plan->t_start, s), "event")) != NSFRB_OK) return st;
-    if ((st = queue_search(plan, d_cube, 0, c.dtype, c.n_t, 0, d_sigma, 0, n_pix, nullptr, nullptr, 0, s)) !=
-        NSFRB_OK)
-        return st;
+    if (mad_slabs_apply(plan))
+        st = queue_search_mad(plan, d_cube, c.dtype, 0, n_pix, s);
+    else
+        st = queue_search(plan, d_cube, 0, c.dtype, c.n_t, 0, d_sigma, 0, n_pix, nullptr, nullptr, 0, s);
+    if (st != NSFRB_OK) return st;
     if (c.dtype != NSFRB_F32 && d_cube_f32 && c.rescore_eps > 0.0f) {
         if ((st = cuda_check(plan,
                              launch_rescore_select(plan->d_rec, n_pix, c.threshold, c.rescore_eps, plan->d_list,
@@ -522,9 +576,12 @@ nsfrb_status nsfrb_search_host(nsfrb_plan_t plan, const void *h_cube, const floa
         if ((st = cuda_check(plan, cudaEventRecord(plan->slab_ev[i], plan->copy_stream), "event")) != NSFRB_OK)
             return st;
         if ((st = cuda_check(plan, cudaStreamWaitEvent(s, plan->slab_ev[i], 0), "wait")) != NSFRB_OK) return st;
-        if ((st = queue_search(plan, plan->d_hcube, 0, c.dtype, c.n_t, 0, h_sigma ? plan->d_hsigma : nullptr, p0,
-                               n, nullptr, nullptr, 0, s)) != NSFRB_OK)
-            return st;
+        if (mad_slabs_apply(plan))
+            st = queue_search_mad(plan, plan->d_hcube, c.dtype, p0, n, s);
+        else
+            st = queue_search(plan, plan->d_hcube, 0, c.dtype, c.n_t, 0, h_sigma ? plan->d_hsigma : nullptr, p0, n,
+                              nullptr, nullptr, 0, s);
+        if (st != NSFRB_OK) return st;
     }
     return queue_finish(plan, s);
 }
@@ -622,6 +679,8 @@ void nsfrb_destroy(nsfrb_plan_t plan) {
     cudaFree(plan->d_counts);
     cudaFree(plan->d_list);
     cudaFree(plan->d_full_snr);
+    cudaFree(plan->d_madws);
+    cudaFree(plan->d_bad);
     cudaFree(plan->d_full_t);
     cudaFree(plan->d_hcube);
     cudaFree(plan->d_hsigma);

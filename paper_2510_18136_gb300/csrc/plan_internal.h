@@ -34,6 +34,9 @@ struct nsfrb_plan_s {
     int32_t *d_counts = nullptr;   // [n_blocks] | err | n_cand | n_list | spare
     int32_t *d_err = nullptr, *d_ncand = nullptr, *d_nlist = nullptr;
     int32_t *d_list = nullptr;
+    float *d_madws = nullptr;      // MAD mode: normalised FP32 slab [mad_slab][n_sub][n_t]
+    uint8_t *d_bad = nullptr;      //   and the per-pixel zero-MAD flags [n_pix]
+    int64_t mad_slab = 0;
     float *d_full_snr = nullptr;
     int16_t *d_full_t = nullptr;
     cudaEvent_t done = nullptr;

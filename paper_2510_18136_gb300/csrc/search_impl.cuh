@@ -1328,6 +1328,10 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel_pipe(const __grid_c
                     if (r.snr > best.snr) best = r;
                 }
                 if (best.dm_idx >= 0) best.dm_idx = s_info[best.dm_idx * kInfo + UI_FIRST_D];
+                if (p.bad_pix && p.bad_pix[pix]) {
+                    best = PixRec{neg_inf(), -1, -1, -1};
+                    atomicOr(p.err, ERR_ZERO_MAD);
+                }
                 p.rec[pix] = best;
                 s_cnt[b] = 0;
             }

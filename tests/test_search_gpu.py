@@ -249,3 +249,38 @@ def test_records_mode_parity(native, dtype, n_t):
     parity.compare_best(snr, idx, best)
     parity.compare_candidates(cand, best, cfg.threshold, np.arange(cfg.n_pix), cfg.nx)
     assert len(cand) > 0
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "f16"])
+@pytest.mark.parametrize("n_t", [840, 1200])
+def test_records_mode_mad_parity(native, dtype, n_t):
+    """MAD normalisation with per-pixel records: the normalisation pass into FP32 slabs and the
+    barrier-free search of them, against the FP64 oracle's median / MAD normalisation of the stored
+    values; a pixel with a constant subband row (zero MAD) is reported and gets no record."""
+    cfg = synth.config_stress(6, 7, n_t=n_t)
+    cfg.widths = np.array([w for w in cfg.widths if w <= n_t], np.int32)
+    cube = synth.beam_student_noise(cfg, 17, dtype=torch.float32)
+    raw = synth.draw_injections(cfg, 5, 18, dm_range=(0.0, 4000.0), max_width=n_t, min_sep=2)
+    sh = oracle.delay_table(cfg.freq_mhz, raw["dm"])
+    inj = synth.place_injections(raw, sh, cfg.n_t, cfg.n_sub,
+                                 synth.beam_sigma(cfg)[raw["row"] * cfg.nx + raw["col"]])
+    synth.add_injections(cube, cfg, inj, sh)
+    tdt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[dtype]
+    cube = cube.to(tdt)
+    good = cube.clone()
+    cube[11, 4, :] = 1.5                                   # zero MAD in one row of pixel 11
+    plan = native.Plan(cfg, dtype=dtype, noise="mad")
+    plan.search(cube.cuda())
+    with pytest.raises(native.NsfrbError) as e:
+        plan.candidates()
+    assert e.value.status == native.EINVAL
+    snr, idx = plan.best()
+    assert snr[11] == -np.inf and (idx[11] == -1).all()
+    plan.search(good.cuda())
+    cand = plan.candidates()
+    snr, idx = plan.best()
+    plan.close()
+    tab, res, best, bad = _oracle(cfg, good.float().numpy(), mad=True)
+    assert bad == 0
+    parity.compare_best(snr, idx, best)
+    parity.compare_candidates(cand, best, cfg.threshold, np.arange(cfg.n_pix), cfg.nx)
