@@ -36,6 +36,7 @@ namespace nsfrb {
 namespace dev {
 
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kHistBinsPerLane = kHistBins / 32;
 __device__ __forceinline__ float neg_inf() { return __int_as_float(0xff800000); }
 __device__ __forceinline__ float qnan() { return __int_as_float(0x7fffffff); }
 

@@ -284,3 +284,32 @@ def test_records_mode_mad_parity(native, dtype, n_t):
     assert bad == 0
     parity.compare_best(snr, idx, best)
     parity.compare_candidates(cand, best, cfg.threshold, np.arange(cfg.n_pix), cfg.nx)
+
+
+@pytest.mark.parametrize("kind", ["ties", "sorted", "spikes"])
+def test_records_mode_mad_order_statistics(native, kind):
+    """Rows that stress the exact median / MAD selection of the normalisation pass: few distinct
+    values (long runs of ties), sorted rows, and constant rows with a few spikes (MAD from the
+    ties of a single value), against the FP64 oracle's sort-based median and MAD."""
+    cfg = synth.SearchConfig(ny=4, nx=5, n_t=1000, dm=np.linspace(0.0, 3000.0, 40),
+                             widths=np.array([1, 2, 4, 8, 32, 100, 640], np.int32), threshold=4.0)
+    rng = np.random.default_rng({"ties": 1, "sorted": 2, "spikes": 3}[kind])
+    shape = (cfg.n_pix, cfg.n_sub, cfg.n_t)
+    if kind == "ties":
+        x = rng.integers(-3, 4, shape).astype(np.float32) * 0.5
+    elif kind == "sorted":
+        x = np.sort(rng.standard_normal(shape).astype(np.float32), axis=2)
+        x[::2] = x[::2, :, ::-1]
+    else:
+        x = np.full(shape, 1.25, np.float32) + rng.integers(0, 4, shape).astype(np.float32) * 0.5
+        x[:, :, rng.integers(0, cfg.n_t, 40)] += 9.0
+    cube = torch.from_numpy(x).to(torch.bfloat16)
+    plan = native.Plan(cfg, dtype="bf16", noise="mad")
+    plan.search(cube.cuda())
+    cand = plan.candidates()
+    snr, idx = plan.best()
+    plan.close()
+    tab, res, best, bad = _oracle(cfg, cube.float().numpy(), mad=True)
+    assert bad == 0
+    parity.compare_best(snr, idx, best)
+    parity.compare_candidates(cand, best, cfg.threshold, np.arange(cfg.n_pix), cfg.nx)
