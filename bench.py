@@ -51,9 +51,13 @@ def parse():
                     help="blocks per field pushed at the 3.355 s cadence (0: skip)")
     ap.add_argument("--bf16-steps", type=int, default=5,
                     help="timed BF16 searches of the bench cube, with and without re-score (0: skip)")
-    ap.add_argument("--classifier-samples", type=int, default=6000,
-                    help="labelled cutouts for the classifier section (0: skip)")
-    ap.add_argument("--classifier-epochs", type=int, default=2)
+    ap.add_argument("--classifier-samples", type=int, default=24000,
+                    help="cutouts made on the fly and trained on once each in the classifier section (0: skip)")
+    ap.add_argument("--classifier-eval-cubes", type=int, default=60,
+                    help="fresh cubes the trained classifier is scored on")
+    ap.add_argument("--campaigns", type=int, default=1,
+                    help="injection campaigns (FN/FP versus threshold, detection rate with and without the "
+                         "classifier) after the classifier section (0: skip)")
     ap.add_argument("--only", default="all", choices=["all", "imager"],
                     help="imager: run only the imager section (one JSON object) and exit")
     ap.add_argument("--imager-steps", type=int, default=20,
@@ -520,25 +524,29 @@ def clf_flops_per_sample(d=32, h=32, w=32, c0=16, c=(32, 32, 64, 64)):
     return fwd, 2 * fwd + dx
 
 
-def classifier_section(native, n_samples: int, epochs: int, seed: int = 0):
-    """Train the candidate classifier on search-produced cutouts; report rates and throughput."""
+def classifier_section(native, n_samples: int, eval_cubes: int, seed: int = 0):
+    """Train the candidate classifier on cutouts made on the fly by the search (each seen once),
+    then score recall and artefact pass rate on fresh cubes; returns (JSON section, classifier)."""
     import torch
     from paper_2510_18136_gb300 import clfdata
     cfg = clfdata.search_config()
-    t0 = time.perf_counter()
-    x, y, _ = clfdata.dataset(n_samples, seed=100 + seed)
-    t_data = time.perf_counter() - t0
+    gen_cfg = clfdata.search_config(256, 256)          # 64 sources per cube for the training stream
     clf = native.Classifier(batch=64, dropout=0.5, seed=7 + seed, lr=1e-3)
     clfdata.init_params(clf, seed=3 + seed)
-    clfdata.train(clf, x, y, epochs=1, seed=seed)          # warm-up epoch
+    t0 = time.perf_counter()
+    losses, seen, t_data = clfdata.train_streaming(clf, n_samples, chunk=6000, seed=100 + seed, cfg=gen_cfg)
+    t_all = time.perf_counter() - t0
+    # training throughput on one resident batch set (no data generation in the timed loop)
+    x, y, _ = clfdata.dataset(2048, seed=77 + seed, cfg=gen_cfg)
+    clfdata.train(clf, x, y, epochs=1, seed=seed)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    losses = clfdata.train(clf, x, y, epochs=epochs, seed=seed + 1)
+    clfdata.train(clf, x, y, epochs=3, seed=seed + 1)
     e1.record()
     torch.cuda.synchronize()
     t_train = e0.elapsed_time(e1) / 1e3
-    n_seen = epochs * (x.shape[0] // clf.batch) * clf.batch
+    n_timed = 3 * (x.shape[0] // clf.batch) * clf.batch
     i0, i1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     xb = x[:clf.batch].contiguous()
     clf.infer(xb)
@@ -548,22 +556,44 @@ def classifier_section(native, n_samples: int, epochs: int, seed: int = 0):
     i1.record()
     torch.cuda.synchronize()
     t_inf = i0.elapsed_time(i1) / 1e3
-    ev = clfdata.evaluate(clf, cfg, range(9000 + 100 * seed, 9012 + 100 * seed))
+    ev = clfdata.evaluate(clf, cfg, range(900000 + 1000 * seed, 900000 + 1000 * seed + eval_cubes))
     thr = clfdata.rates(ev["label"], ev["detected"])
     c15 = clfdata.rates(ev["label"], ev["detected"], ev["p_rfi"], 0.15)
     c50 = clfdata.rates(ev["label"], ev["detected"], ev["p_rfi"], 0.5)
     fwd, train_f = clf_flops_per_sample()
     pk = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"bf16_tflops": 1900.0}
-    train_tflops = n_seen * train_f / t_train / 1e12
-    clf.close()
+    train_tflops = n_timed * train_f / t_train / 1e12
     return {"cutout": "32x32 px x 16 subbands x 32 samples (bf16)", "net": "4 conv (16-32-32-64-64) + FC 32 + FC 1",
-            "train_samples": int(x.shape[0]), "epochs_timed": epochs, "final_loss": losses[-1],
-            "train_samples_per_s": n_seen / t_train, "train_conv_tflops": train_tflops,
+            "trained_on": int(seen), "data": "made on the fly, each cutout seen once (256x256 cubes, 50/50 bursts "
+            "and artefacts)", "first_loss": losses[0], "final_loss": losses[-1], "data_gen_s": t_data,
+            "stream_wall_s": t_all, "train_samples_per_s": n_timed / t_train, "train_conv_tflops": train_tflops,
             "train_tensor_frac_of_bf16_peak": train_tflops / float(pk["bf16_tflops"]),
-            "infer_cutouts_per_s": 20 * clf.batch / t_inf, "data_gen_s": t_data,
+            "infer_cutouts_per_s": 20 * clf.batch / t_inf, "eval_cubes": eval_cubes,
             "threshold_only": thr, "with_classifier_p_lt_0.15": c15, "with_classifier_p_lt_0.5": c50,
-            "threshold_method": "GPU search (parity with the FP64 oracle is a test)"}
+            "threshold_method": "GPU search (parity with the FP64 oracle is a test)"}, clf
+
+
+def campaigns_section(native, clf, seed: int = 0):
+    """Sec. 3.1-3.2 injection campaigns through the GPU search: FN / FP rates against the threshold
+    0-20 and its optimum; detection rate per input S/N 1-40 (50 per bin); and with the trained
+    classifier at p_rfi < 0.15 and < 0.5 (bursts only, PSF noise)."""
+    from paper_2510_18136_gb300 import campaign
+    t0 = time.perf_counter()
+    th = campaign.threshold_curves(n_inj=1000, n_noise=2000, seed=10 + seed)
+    det = campaign.detection_curve(snr_bins=np.arange(1, 41), n_per_bin=50, seed=11 + seed)
+    out = {"threshold_scan": {"thresholds": [float(t) for t in th["thresholds"][::4]],
+                              "fn": [float(v) for v in th["fn"][::4]], "fp": [float(v) for v in th["fp"][::4]],
+                              "optimum": th["optimum"], "injections": 1000, "noise_realisations": 2000,
+                              "injection_snr": "U(0, 10)", "image": "32x32 px x 64 samples, 16 DM 0-4000, widths 1-16"},
+           "detection_rate": {"snr_bins": [float(v) for v in det["snr_bins"]], "rate": [float(v) for v in det["rate"]],
+                              "per_bin": 50, "threshold": 6.0}}
+    if clf is not None:
+        dc = campaign.detection_curve_classified(clf, snr_bins=np.arange(2, 41, 2), cubes_per_bin=3, seed=12 + seed)
+        out["detection_rate_classified"] = {k: (list(map(float, v)) if not isinstance(v, str) else v)
+                                            for k, v in dc.items()}
+    out["wall_s"] = time.perf_counter() - t0
+    return out
 
 
 # ----------------------------------------------------------------------------- imager
@@ -734,9 +764,17 @@ def main():
     elem = 4 if args.dtype == "f32" else 2
     alg_bytes = cfg.n_pix * cfg.n_sub * cfg.n_t * elem + cfg.n_pix * 4 + cfg.n_pix * 16
 
+    # N ranks: the image is N 301-row bands (shard.row_bands of an (N ny) x nx field), one per GPU,
+    # each band's candidates gathered to rank 0 and merged in pixel order every step (weak scaling)
+    from paper_2510_18136_gb300 import shard
+    band = shard.row_bands(cfg.ny * world, world)[rank]
+
     def step():
         plan.search(cube, sigma, stream=stream)
-        return plan.candidates()
+        c = plan.candidates()
+        if world > 1:
+            shard.gather_candidates(c, band, cfg.nx, dst=0)
+        return c
 
     for _ in range(max(3, args.warmup)):
         cand = step()
@@ -795,9 +833,14 @@ def main():
         serving = serving_latency(native, synth, args.serving_blocks, args.serving_paced_blocks, seed=args.seed)
         if args.serving_minutes > 0:
             serving["injection_run"] = serving_injections(native, synth, args.serving_minutes, seed=args.seed)
-    classifier = None
+    classifier, campaigns, clf = None, None, None
     if args.classifier_samples > 0 and rank == 0:
-        classifier = classifier_section(native, args.classifier_samples, args.classifier_epochs, seed=args.seed)
+        classifier, clf = classifier_section(native, args.classifier_samples, args.classifier_eval_cubes,
+                                             seed=args.seed)
+    if args.campaigns and rank == 0:
+        campaigns = campaigns_section(native, clf, seed=args.seed)
+    if clf is not None:
+        clf.close()
 
     imager = None
     if args.imager_steps > 0 and rank == 0:
@@ -820,7 +863,10 @@ def main():
         "config": {"workload": WORKLOAD, "ny": cfg.ny, "nx": cfg.nx, "n_sub": cfg.n_sub, "n_t": cfg.n_t,
                    "n_dm": len(cfg.dm), "n_unique_dm_rows": n_unique, "widths": [int(w) for w in cfg.widths],
                    "storage": args.dtype, "noise": "known sigma", "l2": "inputs larger than L2 (cube "
-                   f"{alg_bytes / 1e9:.2f} GB)", "parallelism": f"replicas x{world} (pixels of one cube per GPU)"},
+                   f"{alg_bytes / 1e9:.2f} GB)",
+                   "parallelism": (f"row bands x{world}: a {cfg.ny * world}x{cfg.nx} image, one {cfg.ny}-row band "
+                                   "per GPU, candidate lists gathered to rank 0 each step" if world > 1 else
+                                   "one GPU")},
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                      "unit": "TFLOP/s", "frac": achieved / peak_ops,
                      "traffic": measured_traffic(cfg.ny, cfg.nx, args.dtype),
@@ -838,6 +884,7 @@ def main():
         "bf16": bf16,
         "serving": serving,
         "classifier": classifier,
+        "campaigns": campaigns,
         "imager": imager,
         "stress": stress,
         "clocks": ck,

@@ -223,6 +223,37 @@ def train(clf: native.Classifier, x: torch.Tensor, y: torch.Tensor, epochs: int,
     return losses
 
 
+def train_streaming(clf: native.Classifier, n_total: int, chunk: int = 4000, seed: int = 0, cfg=None,
+                    device="cuda"):
+    """Training on data made on the fly: balanced chunks of about `chunk` cutouts from fresh cubes
+    (cube seeds never reused), each chunk seen once, until n_total cutouts have been trained on.
+    Returns (per-chunk mean losses, cutouts trained on, seconds spent making data)."""
+    import time
+    losses, seen, t_data = [], 0, 0.0
+    k = 0
+    while seen < n_total:
+        t0 = time.perf_counter()
+        x, y, _ = dataset(min(chunk, n_total - seen), seed=seed + 1000003 * k, cfg=cfg, device=device)
+        torch.cuda.synchronize()
+        t_data += time.perf_counter() - t0
+        losses += train(clf, x, y, epochs=1, seed=seed + k)
+        seen += x.shape[0] // clf.batch * clf.batch
+        k += 1
+        del x, y
+    return losses, seen, t_data
+
+
+def wilson(k: int, n: int, z: float = 1.96):
+    """Wilson score interval of a binomial proportion k / n (None for n = 0)."""
+    if n == 0:
+        return None
+    p = k / n
+    d = 1.0 + z * z / n
+    c = (p + z * z / (2 * n)) / d
+    h = z * math.sqrt(p * (1 - p) / n + z * z / (4 * n * n)) / d
+    return [max(0.0, c - h), min(1.0, c + h)]
+
+
 def p_rfi(clf: native.Classifier, x: torch.Tensor) -> np.ndarray:
     """Sigmoid of the classifier logit for every cutout (inference mode)."""
     B = clf.batch
@@ -280,11 +311,14 @@ def evaluate(clf: native.Classifier, cfg, seeds, device="cuda", taus=(0.15, 0.5)
 
 
 def rates(label, detected, p_rfi=None, tau=None):
-    """Recall on astrophysical sources and false-positive rate on artefacts."""
+    """Recall on astrophysical sources and false-positive rate on artefacts, with their counts and
+    95 % Wilson intervals."""
     ok = detected.copy()
     if tau is not None:
         ok = ok & (np.nan_to_num(p_rfi, nan=1.0) < tau)
     real, art = label == 0, label == 1
+    k_r, k_a = int(ok[real].sum()), int(ok[art].sum())
     return {"recall": float(ok[real].mean()) if real.any() else float("nan"),
             "fpr": float(ok[art].mean()) if art.any() else float("nan"),
-            "n_real": int(real.sum()), "n_artefact": int(art.sum())}
+            "n_real": int(real.sum()), "n_artefact": int(art.sum()), "recovered": k_r, "passed_artefacts": k_a,
+            "recall_95": wilson(k_r, int(real.sum())), "fpr_95": wilson(k_a, int(art.sum()))}

@@ -47,8 +47,13 @@ def test_threshold_campaign_snr_matches_oracle(native):
 
 
 def test_detection_rate_curve(native):
-    r = campaign.detection_curve(snr_bins=np.arange(1, 21), n_per_bin=50, seed=4)
+    """Sec. 3.2: 50 injections per input S/N bin from 1 to 40 sigma."""
+    r = campaign.detection_curve(snr_bins=np.arange(1, 41), n_per_bin=50, seed=4)
     rate = r["rate"]
+    assert len(rate) == 40
     assert rate[:2].max() <= 0.1          # 1-2 sigma injections are almost never above 6
     assert rate[11:].min() >= 0.95        # from 12 sigma on nearly all are found
-    assert rate[-1] == 1.0
+    assert (rate[19:] == 1.0).all()
+    # the recovered S/N of bright injections tracks the input (matched filter on the trial grid)
+    det = r["det_snr"].reshape(40, 50)
+    assert np.median(det[-1]) == pytest.approx(40.0, rel=0.2)

@@ -44,12 +44,19 @@ def _oracle_detect(cfg, seed, truth):
     return det
 
 
-def test_classifier_rejects_artefacts_at_small_recall_cost(native):
-    cfg = clfdata.search_config()
+@pytest.fixture(scope="module")
+def trained(native):
     x, y, _ = clfdata.dataset(6000, seed=100)
     clf = native.Classifier(batch=64, dropout=0.5, seed=7, lr=1e-3)
     clfdata.init_params(clf, seed=3)
     losses = clfdata.train(clf, x, y, epochs=4)
+    yield clf, losses
+    clf.close()
+
+
+def test_classifier_rejects_artefacts_at_small_recall_cost(native, trained):
+    cfg = clfdata.search_config()
+    clf, losses = trained
     assert losses[-1] < losses[0]
     ev = clfdata.evaluate(clf, cfg, range(9000, 9012))
     det_oracle = np.concatenate([_oracle_detect(cfg, s, t) for s, t in ev["cubes"]])
@@ -64,4 +71,20 @@ def test_classifier_rejects_artefacts_at_small_recall_cost(native):
     assert c50["fpr"] < 0.5 * thr["fpr"]
     assert c50["recall"] > 0.7 * thr["recall"]
     assert c15["fpr"] <= c50["fpr"] and c15["recall"] <= c50["recall"]
-    clf.close()
+    lo, hi = c50["recall_95"]
+    assert lo <= c50["recall"] <= hi and c50["n_real"] == int((ev["label"] == 0).sum())
+
+
+def test_detection_curve_with_classifier(native, trained):
+    """Sec. 3.2 detection rate per S/N bin, threshold alone and behind the classifier (bursts only):
+    the classifier passes a subset of the threshold detections, most of them at high S/N, and the
+    rate rises with S/N."""
+    from paper_2510_18136_gb300 import campaign
+    clf, _ = trained
+    bins = np.array([4, 8, 12, 20, 30, 40])
+    r = campaign.detection_curve_classified(clf, snr_bins=bins, cubes_per_bin=2, seed=5)
+    thr, c15, c50 = np.array(r["threshold"]), np.array(r["p<0.15"]), np.array(r["p<0.5"])
+    print("threshold", thr, "p<0.15", c15, "p<0.5", c50)
+    assert (c15 <= c50 + 1e-12).all() and (c50 <= thr + 1e-12).all()
+    assert thr[0] < thr[2] and thr[-1] >= 0.95
+    assert c50[3:].min() >= 0.6 * thr[3:].min()
