@@ -258,7 +258,8 @@ nsfrb_status nsfrb_search_static(nsfrb_plan_t plan, const void *d_cube, const fl
  * present_mask are zero-filled for that block.
  * Re-scoring (16-bit storage with cfg.rescore_eps > 0): the stream also keeps
  * the window in FP32 in pinned host memory (ny*nx*n_sub*n_t*4 bytes, mapped,
- * written by the device as blocks arrive); after each block the pixels whose
+ * written by the device as blocks arrive, sample plane by sample plane in the
+ * block's [n_sub][ny][nx] layout); after each block the pixels whose
  * best S/N over the new trials lies within +-rescore_eps of the threshold are
  * searched again from it in FP32 (same new-trial mask) before the candidate
  * list is formed. */

@@ -57,6 +57,9 @@ struct SearchParams {
     const int32_t *t_off_dev;   // if set, t_off is read from device memory
     int32_t t_wrap;        // > 0: a row is a ring of t_wrap samples, window sample t sits at
                            // (t_off + t) mod t_wrap (t_off < t_wrap; plain loads only)
+    int64_t t_stride;      // > 0 (plain loads only): a sample-major cube, element (pixel q,
+                           // subband k, ring position j) at cube[(j * n_sub + k) * t_stride + q],
+                           // t_stride the pixel count of a sample plane
     int32_t dtype;         // NSFRB_F32 / BF16 / F16
     int32_t n_sub, n_t;
     int32_t Tp;            // shared-memory row pitch (floats)
@@ -87,6 +90,8 @@ struct SearchParams {
     int32_t n_dm;
     int32_t new_blk;       // > 0: only trials that end in the last new_blk samples
     int32_t pipe;          // 1: barrier-free kernel (stage 1 or 3, KNOWN noise, records only)
+    int32_t teams;         // barrier-free kernel: 1 (all warps on one pixel at a time) or 2 (two
+                           // teams of half the warps, each on its own pixel with its own buffers)
     // ---- outputs (indexed by absolute pixel)
     PixRec *rec;
     float *full_snr;       // [pix][n_dm][n_w] or nullptr
@@ -109,7 +114,8 @@ __host__ __device__ inline SmemLayout smem_layout(const SearchParams &p, int C) 
     L.table = o;
     o += align_up(sizeof(int32_t) * ((size_t)p.n_u * kInfo + p.n_deltas + (size_t)p.n_u * p.n_sub), 16);
     L.xs = o;
-    const int nbuf = (p.stage == 1 || p.stage == 3) ? 2 : 1;
+    const int teams = (p.pipe && p.teams > 1) ? p.teams : 1;
+    const int nbuf = (p.stage == 1 || p.stage == 3) ? 2 * teams : 1;
     const size_t es = (p.stage == 3) ? 2 : sizeof(float);
     o += align_up(es * (size_t)nbuf * p.n_sub * p.Tp, 128);
     L.stg = o;
@@ -120,13 +126,14 @@ __host__ __device__ inline SmemLayout smem_layout(const SearchParams &p, int C) 
     // MAD histograms: in the staging buffer of the current item when staging, else own space
     if (p.noise_mode == 1 && p.stage != 2) o += sizeof(uint32_t) * (size_t)kWarps * kHistBins;
     L.wbest = o;
-    const size_t n_slots = p.pipe ? 2 : 1;   // the barrier-free kernel keeps two pixels' records
+    // the barrier-free kernel keeps two pixels' records per team
+    const size_t n_slots = p.pipe ? 2 * static_cast<size_t>(teams) : 1;
     o += sizeof(PixRec) * kWarps * n_slots;
     L.sinv = o;
-    o += sizeof(float) * kMaxW * n_slots + sizeof(int32_t) * 4;
+    o += sizeof(float) * kMaxW * n_slots + sizeof(int32_t) * (2 * n_slots + 4);
     o = align_up(o, 8);
     L.bar = o;
-    o += sizeof(unsigned long long) * 2;
+    o += sizeof(unsigned long long) * 2 * teams;
     L.total = o;
     return L;
 }

@@ -113,7 +113,8 @@ bool choose_stage_for(int C, int max_smem, SearchParams &sp, size_t &smem) {
     // The barrier-free kernel: rows bulk-copied as stored (FP32, or 16-bit read in place, which
     // needs the sample-pair path of even chunks), KNOWN noise, per-pixel records only.  The copy
     // starts at the 16-byte boundary at or below the window start and must stay inside the row.
-    if (sp.t_wrap == 0 && sp.noise_mode == 0 && !sp.full_snr && (sp.dtype == NSFRB_F32 || C % 2 == 0) &&
+    if (sp.t_wrap == 0 && sp.t_stride == 0 && sp.noise_mode == 0 && !sp.full_snr &&
+        (sp.dtype == NSFRB_F32 || C % 2 == 0) &&
         base % 16 == 0 && sp.row_len % epv == 0) {
         bool fits_row;
         if (sp.t_off_dev)   // a ring row: the window start is below n_t, the row 2 n_t + 8 long
@@ -127,17 +128,23 @@ bool choose_stage_for(int C, int max_smem, SearchParams &sp, size_t &smem) {
             sp.stage = (sp.dtype == NSFRB_F32) ? 1 : 3;
             sp.stg_pitch = 0;
             sp.pipe = 1;
-            const SmemLayout L = smem_layout(sp, C);
-            if (L.total <= static_cast<size_t>(max_smem)) {
-                smem = L.total;
-                return true;
+            // two teams (each on its own pixel, half the row groups to build from scratch) where two
+            // double buffers fit, else one
+            for (int teams = 2; teams >= 1; --teams) {
+                sp.teams = teams;
+                const SmemLayout L = smem_layout(sp, C);
+                if (L.total <= static_cast<size_t>(max_smem)) {
+                    smem = L.total;
+                    return true;
+                }
             }
         }
+        sp.teams = 1;
     }
     sp.pipe = 0;
     int want = 0;
-    if (sp.t_wrap > 0) {
-        want = 0;   // ring rows: plain loads with the wrap-around index
+    if (sp.t_wrap > 0 || sp.t_stride > 0) {
+        want = 0;   // ring rows or sample-major cubes: plain loads
     } else if (sp.dtype == NSFRB_F32) {
         // bulk copies start at the window start: 16-byte aligned only if it is a multiple of 4
         // samples.  A window start kept on the device (serving) moves by new_blk per block.
@@ -225,7 +232,7 @@ nsfrb_status ensure_device(nsfrb_plan_s *pl) {
 nsfrb_status queue_search(nsfrb_plan_s *pl, const void *cube, int64_t cube_pix0, int dtype, int64_t row_len,
                           int t_off, const float *sigma, int64_t pix0, int64_t n, const int32_t *pix_list,
                           const int32_t *n_items_dev, int new_blk, cudaStream_t s, const int32_t *t_off_dev,
-                          int t_wrap) {
+                          int t_wrap, int64_t t_stride) {
     SearchParams sp;
     base_params(pl, sp);
     sp.cube = cube;
@@ -235,6 +242,7 @@ nsfrb_status queue_search(nsfrb_plan_s *pl, const void *cube, int64_t cube_pix0,
     sp.t_off = t_off;
     sp.t_off_dev = t_off_dev;
     sp.t_wrap = t_wrap;
+    sp.t_stride = t_stride;
     sp.sigma = sigma;
     sp.pix0 = pix0;
     sp.n_items = n;

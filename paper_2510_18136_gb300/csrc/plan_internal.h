@@ -57,8 +57,8 @@ struct nsfrb_plan_s {
     void *d_ring = nullptr;
     float *d_blk = nullptr;        // [n_blk][n_sub][n_pix] FP32 block on the device
     int32_t *d_sstate = nullptr;   // [0] window start in the ring row, [1] samples written mod n_t
-    float *h_fring = nullptr;      // re-score: host-pinned FP32 window [n_pix][n_sub][n_t], a ring of
-    float *d_fring = nullptr;      //   n_t samples per row (mapped; d_fring is its device address)
+    float *h_fring = nullptr;      // re-score: host-pinned FP32 window [n_t][n_sub][n_pix], a ring of
+    float *d_fring = nullptr;      //   n_t sample planes (mapped; d_fring is its device address)
     cudaStream_t s_stream = nullptr;
     cudaGraphExec_t s_graph = nullptr;
     cudaEvent_t s_ev_push = nullptr, s_ev_done = nullptr;
@@ -78,7 +78,7 @@ nsfrb_status ensure_device(nsfrb_plan_s *pl);
 nsfrb_status queue_search(nsfrb_plan_s *pl, const void *cube, int64_t cube_pix0, int dtype, int64_t row_len,
                           int t_off, const float *sigma, int64_t pix0, int64_t n, const int32_t *pix_list,
                           const int32_t *n_items_dev, int new_blk, cudaStream_t s,
-                          const int32_t *t_off_dev = nullptr, int t_wrap = 0);
+                          const int32_t *t_off_dev = nullptr, int t_wrap = 0, int64_t t_stride = 0);
 size_t elem_size(int dtype);
 void destroy_stream_state(nsfrb_plan_s *pl);
 void base_params(const nsfrb_plan_s *pl, SearchParams &sp);

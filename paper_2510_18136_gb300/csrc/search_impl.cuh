@@ -256,6 +256,24 @@ __device__ __forceinline__ int generic_find(const float *Pw, int w, int L, int t
     return INT_MAX;
 }
 
+// Serving (at most 32 new trial ends per width): lane j takes the trial t = t_lo + j, with no loop
+// and no branch; lanes past the last trial give -inf.
+__device__ __forceinline__ float masked_max32(const float *Pw, int w, int L, int t_lo, int lane) {
+    const int t = t_lo + lane;
+    const bool ok = t + w <= L;
+    const int ti = ok ? t : 0;
+    const float b = Pw[ti + (ok ? w : 0)] - Pw[ti];
+    return ok ? b : neg_inf();
+}
+
+__device__ __forceinline__ int masked_find32(const float *Pw, int w, int L, int t_lo, int lane, float inv, float target) {
+    const int t = t_lo + lane;
+    const bool ok = t + w <= L;
+    const int ti = ok ? t : 0;
+    const float b = Pw[ti + (ok ? w : 0)] - Pw[ti];
+    return (ok && b * inv == target) ? t : INT_MAX;
+}
+
 #define NSFRB_POW2(X) X(0) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10)
 
 // In-lane prefix of this lane's chunk: Lp[c] = D[0] + ... + D[c-1]; returns the total.
@@ -784,7 +802,9 @@ __device__ __forceinline__ int find_t_even(const SearchParams &p, const float2 (
     constexpr int SH = (C < kSmallMax) ? C : kSmallMax;
     const int w = p.widths[wi];
     int t;
-    if (masked || p.wclass[wi] == WC_GENERIC) {
+    if (masked && p.new_blk <= 32) {
+        t = masked_find32(Pw, w, L, max(0, L - w - p.new_blk + 1), lane, inv, target);
+    } else if (masked || p.wclass[wi] == WC_GENERIC) {
         const int tl = masked ? max(0, L - w - p.new_blk + 1) : 0;
         t = generic_find(Pw, w, L, tl, lane, inv, target);
     } else if (p.wclass[wi] == WC_SMALL) {
@@ -904,8 +924,21 @@ __device__ __forceinline__ PixRec search_rows_even(const SearchParams &p, const 
             NSFRB_POW2(NSFRB_LARGE_PK)
 #undef NSFRB_LARGE_PK
         }
-        // every other width (and every width of a masked search) from shared memory
-        const int n_gen = masked ? p.n_w : p.n_gen;
+        if (masked && p.new_blk <= 32) {
+            // serving: every width's trials that end in the newest block, one per lane; ascending
+            // width order with a strict '>' keeps the smallest width index on ties
+#pragma unroll 4
+            for (int wi = 0; wi < p.n_w; ++wi) {
+                const int w = p.widths[wi];
+                const float s = masked_max32(Pw, w, L, max(0, L - w - p.new_blk + 1), lane) * s_inv[wi];
+                if (s > ls) {
+                    ls = s;
+                    lw = wi;
+                }
+            }
+        }
+        // every other width (and every width of a masked search of longer blocks) from shared memory
+        const int n_gen = masked ? (p.new_blk <= 32 ? 0 : p.n_w) : p.n_gen;
 #pragma unroll 1
         for (int g = 0; g < n_gen; ++g) {
             const int wi = masked ? g : p.gen_wi[g];
@@ -1065,7 +1098,9 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel(const __grid_consta
                 const int k = i / n_t, t = i - k * n_t;
                 int tt = t_off + t;
                 if (p.t_wrap > 0 && tt >= p.t_wrap) tt -= p.t_wrap;
-                xs[(size_t)k * Tp + t] = load_elem(p.cube, (row0 + k) * p.row_len + tt, p.dtype);
+                const int64_t at = p.t_stride > 0 ? (static_cast<int64_t>(tt) * n_sub + k) * p.t_stride + pix
+                                                  : (row0 + k) * p.row_len + tt;
+                xs[(size_t)k * Tp + t] = load_elem(p.cube, at, p.dtype);
             }
         } else {
             const bool ok = mbar_wait(&s_bar[sb], phase[sb]);
@@ -1202,34 +1237,39 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel(const __grid_consta
 // ------------------------------------------------------------------ barrier-free kernel
 
 // Same search (rows bulk-copied straight into a double buffer, KNOWN noise, per-pixel records only)
-// without CTA barriers between pixels.  Every warp walks the CTA's pixels on its own; on the CTA's
-// i-th pixel warp w takes row group (w + i) mod kWarps, so the groups with one row more rotate over
-// the warps.  A warp publishes its group's best and counts itself done; the last warp of a pixel
-// combines the groups in row order (the DM tie rule), writes the pixel's record, and starts the copy
-// of the pixel two ahead into the buffer it frees (with that pixel's 1 / (sigma sqrt(w))).  Warps
-// drift apart by at most one pixel.
+// without CTA barriers between pixels.  The CTA's warps form TEAMS teams of W = kWarps / TEAMS warps;
+// each team walks its own pixels (items team, team + TEAMS * grid, ... of the CTA) with its own
+// double buffer, so a pixel's distinct DM rows are split into W groups (fewer teams: more groups,
+// each built from scratch; more teams: more pixels in shared memory).  Within a team every warp
+// walks the team's pixels on its own; on the team's i-th pixel warp w takes row group (w + i) mod W,
+// so the groups with one row more rotate over the warps.  A warp publishes its group's best and
+// counts itself done; the last warp of a pixel combines the groups in row order (the DM tie rule),
+// writes the pixel's record, and starts the copy of the team's pixel two ahead into the buffer it
+// frees (with that pixel's 1 / (sigma sqrt(w))).  Warps of a team drift apart by at most one pixel.
 // ST is the storage type of the rows, kept as they are in shared memory: FP32, or BF16 / FP16 read
 // in place by the mixed-precision adds (no widening pass).  A window that starts at any sample t_off
 // is copied from the 16-byte boundary below it and read from element eoff = t_off mod (16 / size)
 // of the staged row; when the copy then carries samples past the window, the de-dispersed samples
 // past the valid range are set to -inf instead of relying on -inf past the window.
-template <int C, int ST>
+template <int C, int ST, int TEAMS>
 __global__ void __launch_bounds__(kThreads, 1) search_kernel_pipe(const __grid_constant__ SearchParams p) {
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr int kEs = (ST == 0) ? 4 : 2;          // bytes per stored sample
     constexpr int kEpv = 16 / kEs;                  // samples per 16 bytes
+    constexpr int W = kWarps / TEAMS;               // warps (and row groups) per team
+    static_assert(kWarps % TEAMS == 0, "teams divide the warps");
     const SmemLayout lay = smem_layout(p, C);
     int32_t *s_table = reinterpret_cast<int32_t *>(smem + lay.table);
     unsigned char *s_xs = smem + lay.xs;
     float *s_pbuf = reinterpret_cast<float *>(smem + lay.pbuf);
-    PixRec *s_wbest = reinterpret_cast<PixRec *>(smem + lay.wbest);        // [2][kWarps] by row group
-    float *s_inv = reinterpret_cast<float *>(smem + lay.sinv);             // [2][kMaxW]
-    int32_t *s_word = reinterpret_cast<int32_t *>(smem + lay.sinv + sizeof(float) * kMaxW * 2);
-    int32_t *s_cnt = s_word;          // [2] warps done with the pixel in each buffer
-    int32_t *s_flag = s_word + 2;     // error seen by a warp
-    unsigned long long *s_bar = reinterpret_cast<unsigned long long *>(smem + lay.bar);
+    PixRec *s_wbest = reinterpret_cast<PixRec *>(smem + lay.wbest);        // [TEAMS][2][kWarps]
+    float *s_inv = reinterpret_cast<float *>(smem + lay.sinv);             // [TEAMS][2][kMaxW]
+    int32_t *s_cnt = reinterpret_cast<int32_t *>(smem + lay.sinv + sizeof(float) * kMaxW * 2 * TEAMS);
+    int32_t *s_flag = s_cnt + 2 * TEAMS;    // error seen by a warp
+    unsigned long long *s_bar = reinterpret_cast<unsigned long long *>(smem + lay.bar);   // [TEAMS][2]
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int team = warp / W, wt = warp % W;
     const int n_sub = p.n_sub, n_t = p.n_t, Tp = p.Tp;
     const int t_off = p.t_off_dev ? *p.t_off_dev : p.t_off;
     const int eoff = t_off & (kEpv - 1);
@@ -1242,8 +1282,8 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel_pipe(const __grid_c
     const int32_t *s_info = s_table;
     const int32_t *s_delta = s_table + p.n_u * kInfo;
     const int32_t *s_shift = s_delta + p.n_deltas;
-    // -inf past the copied part of every row of both buffers (never overwritten)
-    for (int b = 0; b < 2; ++b)
+    // -inf past the copied part of every row of every buffer (never overwritten)
+    for (int b = 0; b < 2 * TEAMS; ++b)
         for (int i = tid; i < n_sub * (Tp - row_elems); i += kThreads) {
             const int k = i / (Tp - row_elems), t = row_elems + i % (Tp - row_elems);
             unsigned char *row = s_xs + b * buf_bytes + (size_t)k * Tp * kEs;
@@ -1258,74 +1298,79 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel_pipe(const __grid_c
     auto item_pixel = [&](int64_t it) -> int64_t {
         return p.pix_list ? static_cast<int64_t>(p.pix_list[it]) : p.pix0 + it;
     };
-    // one warp: 1 / (sigma sqrt(w)) of item `it` into slot b, then its rows into buffer b
+    // slot (team, b): buffer, barrier, records, 1 / (sigma sqrt(w)) and done counter of one pixel
+    const int slot0 = 2 * team;
+    // one warp: 1 / (sigma sqrt(w)) of item `it` into slot s, then its rows into buffer s
     // (lane 0 arms the barrier, lane k copies subband k)
-    auto issue_warp = [&](int64_t it, int b) {
+    auto issue_warp = [&](int64_t it, int sl) {
         const int64_t pix = item_pixel(it);
         if (lane < p.n_w) {
             const float sg = p.sigma ? p.sigma[pix] : p.sigma_default;
-            s_inv[b * kMaxW + lane] = 1.0f / (sg * sqrtf(static_cast<float>(p.widths[lane])));
+            s_inv[sl * kMaxW + lane] = 1.0f / (sg * sqrtf(static_cast<float>(p.widths[lane])));
         }
         __syncwarp();
         const uint32_t bytes = static_cast<uint32_t>(row_elems * kEs);
-        if (lane == 0) mbar_expect_tx(&s_bar[b], bytes * static_cast<uint32_t>(n_sub));
+        if (lane == 0) mbar_expect_tx(&s_bar[sl], bytes * static_cast<uint32_t>(n_sub));
         __syncwarp();
         const unsigned char *src = static_cast<const unsigned char *>(p.cube);
         const int64_t row0 = (pix - p.cube_pix0) * n_sub;
-        unsigned char *dst = s_xs + b * buf_bytes;
+        unsigned char *dst = s_xs + sl * buf_bytes;
         for (int k = lane; k < n_sub; k += 32)
             bulk_g2s(dst + (size_t)k * Tp * kEs, src + ((row0 + k) * p.row_len + t_off - eoff) * kEs, bytes,
-                     &s_bar[b]);
+                     &s_bar[sl]);
     };
     if (tid == 0) {
-        mbar_init(&s_bar[0], 1);
-        mbar_init(&s_bar[1], 1);
-        s_cnt[0] = 0;
-        s_cnt[1] = 0;
+        for (int sl = 0; sl < 2 * TEAMS; ++sl) {
+            mbar_init(&s_bar[sl], 1);
+            s_cnt[sl] = 0;
+        }
         s_flag[0] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_proxy_async();
     }
     __syncthreads();
-    if (warp == 0) {
-        if (blockIdx.x < n_items) issue_warp(blockIdx.x, 0);
-        if (blockIdx.x + gridDim.x < n_items) issue_warp(blockIdx.x + gridDim.x, 1);
+    // the team's items: it0 = CTA * TEAMS + team, then every G = grid * TEAMS
+    const int64_t G = static_cast<int64_t>(gridDim.x) * TEAMS;
+    const int64_t it0 = static_cast<int64_t>(blockIdx.x) * TEAMS + team;
+    if (wt == 0) {
+        if (it0 < n_items) issue_warp(it0, slot0);
+        if (it0 + G < n_items) issue_warp(it0 + G, slot0 + 1);
     }
 
     const int n_ua = p.n_u_active;
     float *Pw = s_pbuf + (size_t)warp * 32 * C;
     int issued_last = -1;   // local index of the last item whose copy this warp started
     int i = 0;
-    for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x, ++i) {
-        const int b = i & 1;
+    for (int64_t it = it0; it < n_items; it += G, ++i) {
+        const int b = i & 1, sl = slot0 + b;
         if (*reinterpret_cast<volatile int32_t *>(s_flag)) break;
-        if (!mbar_wait(&s_bar[b], static_cast<uint32_t>(i >> 1) & 1u)) {
+        if (!mbar_wait(&s_bar[sl], static_cast<uint32_t>(i >> 1) & 1u)) {
             if (lane == 0) {
                 atomicOr(s_flag, ERR_WAIT_TIMEOUT);
                 atomicOr(p.err, ERR_WAIT_TIMEOUT);
             }
             break;
         }
-        const int g = (warp + i) % kWarps;
-        const int u_lo = (g * n_ua) / kWarps, u_hi = ((g + 1) * n_ua) / kWarps;
+        const int g = (wt + i) % W;
+        const int u_lo = (g * n_ua) / W, u_hi = ((g + 1) * n_ua) / W;
         const int64_t pix = item_pixel(it);
-        const PixRec wr = search_rows_any<C, false, ST>(p, s_xs + b * buf_bytes, Pw, s_inv + b * kMaxW, s_info,
+        const PixRec wr = search_rows_any<C, false, ST>(p, s_xs + sl * buf_bytes, Pw, s_inv + sl * kMaxW, s_info,
                                                         s_delta, s_shift, u_lo, u_hi, pix, lane, eoff, mask_tail);
-        // publish; this warp's reads of buffer b are done before the copy that refills it
+        // publish; this warp's reads of buffer sl are done before the copy that refills it
         fence_proxy_async();
         int last = 0;
         if (lane == 0) {
-            s_wbest[b * kWarps + g] = wr;
+            s_wbest[sl * kWarps + g] = wr;
             __threadfence_block();
-            last = atomicAdd(&s_cnt[b], 1) == kWarps - 1;
+            last = atomicAdd(&s_cnt[sl], 1) == W - 1;
             __threadfence_block();
         }
         last = __shfl_sync(kFull, last, 0);
         if (last) {
             if (lane == 0) {
                 PixRec best{neg_inf(), -1, -1, -1};
-                for (int q = 0; q < kWarps; ++q) {
-                    const PixRec r = s_wbest[b * kWarps + q];
+                for (int q = 0; q < W; ++q) {
+                    const PixRec r = s_wbest[sl * kWarps + q];
                     if (r.snr > best.snr) best = r;
                 }
                 if (best.dm_idx >= 0) best.dm_idx = s_info[best.dm_idx * kInfo + UI_FIRST_D];
@@ -1334,12 +1379,12 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel_pipe(const __grid_c
                     atomicOr(p.err, ERR_ZERO_MAD);
                 }
                 p.rec[pix] = best;
-                s_cnt[b] = 0;
+                s_cnt[sl] = 0;
             }
             __syncwarp();
-            const int64_t nxt = it + 2 * (int64_t)gridDim.x;
+            const int64_t nxt = it + 2 * G;
             if (nxt < n_items) {
-                issue_warp(nxt, b);
+                issue_warp(nxt, sl);
                 issued_last = i + 2;
             }
         }
@@ -1347,14 +1392,28 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel_pipe(const __grid_c
     }
     // after an error: wait (bounded) for copies this warp started that may still be in flight
     if (*reinterpret_cast<volatile int32_t *>(s_flag) && lane == 0 && issued_last >= 0)
-        mbar_wait(&s_bar[issued_last & 1], static_cast<uint32_t>(issued_last >> 1) & 1u);
+        mbar_wait(&s_bar[slot0 + (issued_last & 1)], static_cast<uint32_t>(issued_last >> 1) & 1u);
 }
 
 }  // namespace dev
 
 // 16-bit rows read in place need the sample-pair path (even chunks); odd chunks get FP32 only.
 #define NSFRB_PIPE_LAUNCH(CC, ST)                                                              \
-    dev::search_kernel_pipe<CC, ST><<<grid, kThreads, smem, s>>>(p)
+    do {                                                                                       \
+        if (p.teams == 2)                                                                      \
+            dev::search_kernel_pipe<CC, ST, 2><<<grid, kThreads, smem, s>>>(p);                \
+        else                                                                                   \
+            dev::search_kernel_pipe<CC, ST, 1><<<grid, kThreads, smem, s>>>(p);                \
+    } while (0)
+#define NSFRB_PIPE_ATTR(CC, ST)                                                                \
+    do {                                                                                       \
+        if (e == cudaSuccess)                                                                  \
+            e = cudaFuncSetAttribute(dev::search_kernel_pipe<CC, ST, 1>,                       \
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, sm);         \
+        if (e == cudaSuccess)                                                                  \
+            e = cudaFuncSetAttribute(dev::search_kernel_pipe<CC, ST, 2>,                       \
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, sm);         \
+    } while (0)
 #define NSFRB_INSTANTIATE_SEARCH(CC)                                                           \
     cudaError_t launch_search_c##CC(const SearchParams &p, int grid, size_t smem, cudaStream_t s) { \
         if (p.pipe) {                                                                          \
@@ -1383,16 +1442,10 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel_pipe(const __grid_c
         if (e == cudaSuccess)                                                                  \
             e = cudaFuncSetAttribute(dev::search_kernel<CC, true>,                             \
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, sm);         \
-        if (e == cudaSuccess)                                                                  \
-            e = cudaFuncSetAttribute(dev::search_kernel_pipe<CC, 0>,                           \
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, sm);         \
+        NSFRB_PIPE_ATTR(CC, 0);                                                                \
         if constexpr (CC % 2 == 0) {                                                           \
-            if (e == cudaSuccess)                                                              \
-                e = cudaFuncSetAttribute(dev::search_kernel_pipe<CC, 1>,                       \
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, sm);     \
-            if (e == cudaSuccess)                                                              \
-                e = cudaFuncSetAttribute(dev::search_kernel_pipe<CC, 2>,                       \
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, sm);     \
+            NSFRB_PIPE_ATTR(CC, 1);                                                            \
+            NSFRB_PIPE_ATTR(CC, 2);                                                            \
         }                                                                                      \
         return e;                                                                              \
     }

@@ -40,7 +40,8 @@ constexpr int kTrPix = 32;   // pixels per transpose tile
 // subband); the tile is staged through shared memory so that both the reads
 // (along pixels) and the writes (along samples) are contiguous.  With fring
 // (re-score of 16-bit windows) the FP32 values also go to the host-pinned
-// window [n_pix][n_sub][n_t], a ring of n_t samples per row.
+// window [n_t][n_sub][n_pix], a ring of n_t sample planes in the block's own
+// layout, so that those writes are contiguous along pixels too.
 template <typename T>
 __global__ void ingest_kernel(const float *__restrict__ blk, T *__restrict__ ring, int64_t n_pix, int n_sub,
                               int n_blk, int n_t, int64_t ring_len, const int32_t *__restrict__ state,
@@ -49,15 +50,20 @@ __global__ void ingest_kernel(const float *__restrict__ blk, T *__restrict__ rin
     const int k = blockIdx.y;
     const int64_t p0 = static_cast<int64_t>(blockIdx.x) * kTrPix;
     const bool present = (*mask >> k) & 1u;
+    const int wpos = state[1];   // ring position of the block's first sample
     for (int i = threadIdx.x; i < n_blk * kTrPix; i += blockDim.x) {
         const int t = i / kTrPix, j = i % kTrPix;
         const int64_t p = p0 + j;
         float v = 0.0f;
         if (present && p < n_pix) v = blk[(static_cast<int64_t>(t) * n_sub + k) * n_pix + p];
         tile[t * (kTrPix + 1) + j] = v;
+        if (fring && p < n_pix) {
+            int pos = wpos + t;
+            if (pos >= n_t) pos -= n_t;
+            fring[(static_cast<int64_t>(pos) * n_sub + k) * n_pix + p] = v;
+        }
     }
     __syncthreads();
-    const int wpos = state[1];   // ring position of the block's first sample
     for (int i = threadIdx.x; i < n_blk * kTrPix; i += blockDim.x) {
         const int j = i / n_blk, t = i % n_blk;
         const int64_t p = p0 + j;
@@ -69,7 +75,6 @@ __global__ void ingest_kernel(const float *__restrict__ blk, T *__restrict__ rin
         T *row = ring + (p * n_sub + k) * ring_len;
         row[pos] = v;
         row[pos + n_t] = v;
-        if (fring) fring[(p * n_sub + k) * n_t + pos] = f;
     }
 }
 
@@ -218,7 +223,7 @@ nsfrb_status nsfrb_stream_open(nsfrb_plan_t plan, int32_t n_blk, size_t hbm_rese
                         "re-score select");
         if (qs == NSFRB_OK)
             qs = queue_search(plan, plan->d_fring, 0, NSFRB_F32, c.n_t, 0, nullptr, 0, n_pix, plan->d_list,
-                              plan->d_nlist, n_blk, s, plan->d_sstate, c.n_t);
+                              plan->d_nlist, n_blk, s, plan->d_sstate, c.n_t, n_pix);
     }
     if (ok && qs == NSFRB_OK)
         qs = cuda_check(plan,
