@@ -458,6 +458,7 @@ def bf16_section(native, synth, cfg, cube32, sigma, steps: int, e2e_steps: int, 
     out = {"rescore_eps": eps}
     for name, kw, extra in (("plain", {}, {}), ("rescore", {"rescore_eps": eps}, {"cube_f32": cube32})):
         plan = native.Plan(cfg, dtype="bf16", **kw)
+        tile, tile_ms = plan.autotune(cube16, sigma, reps=3, stream=stream)
         for _ in range(3):
             plan.search(cube16, sigma, stream=stream, **extra)
             cand = plan.candidates()
@@ -468,7 +469,7 @@ def bf16_section(native, synth, cfg, cube32, sigma, steps: int, e2e_steps: int, 
             ks.append(plan.last_timing()[0])
         snr, _ = plan.best()
         out[name] = {"kernel_ms": statistics.median(ks), "trials_per_s": cfg.n_trials / (statistics.median(ks) / 1e3),
-                     "candidates": int(len(cand))}
+                     "candidates": int(len(cand)), "tile": tile, "tile_ms": tile_ms}
         if name == "plain":
             fin = np.isfinite(s32)
             err = np.abs(snr[fin].astype(np.float64) - s32[fin])
@@ -488,6 +489,7 @@ def bf16_section(native, synth, cfg, cube32, sigma, steps: int, e2e_steps: int, 
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             p2 = native.Plan(cfg, dtype="bf16")
+            p2.set_tile(native.BF16, tile)
             p2.search_host(host, hs, stream=stream)
             p2.candidates()
             e0.record(stream)
@@ -674,6 +676,7 @@ def stress_section(native, synth, steps: int, seed: int = 0):
     torch.cuda.empty_cache()
     plan = native.Plan(cfg, dtype="bf16", noise="mad")
     stream = torch.cuda.current_stream()
+    tile, tile_ms = plan.autotune(cube, reps=2, stream=stream)   # tile of the FP32 slab search
     ops, n_unique = alg_ops(cfg, plan)
     for _ in range(2):
         plan.search(cube, stream=stream)
@@ -726,7 +729,7 @@ def stress_section(native, synth, steps: int, seed: int = 0):
             "false_alarm_pixels_above_7.2": fa72,
             "roofline": {"bound": "alu", "achieved": ops / tk / 1e12, "peak": peak_ops / 1e12, "unit": "TFLOP/s",
                          "frac": ops / tk / peak_ops, "kernel": f"{search_kernel_name(cfg.n_t, 'bf16', 'mad')} (MAD normalisation)",
-                         "kernel_ms": tk * 1e3, "ops_per_launch": ops},
+                         "kernel_ms": tk * 1e3, "ops_per_launch": ops, "tile": tile, "tile_ms": tile_ms},
             "hbm": {"achieved_gbs": alg_bytes / tk / 1e9, "frac": alg_bytes / tk / 1e9 / pk["hbm_gbs"],
                     "bytes_per_launch": alg_bytes},
             "l2": f"inputs larger than L2 (cube {alg_bytes / 1e9:.1f} GB)"}
@@ -760,6 +763,8 @@ def main():
     sigma = torch.full((cfg.n_pix,), cfg.sigma_pix * math.sqrt(cfg.n_sub), device=dev)
     plan = native.Plan(cfg, dtype=args.dtype)
     stream = torch.cuda.current_stream()
+    # pixel x DM tile of the search kernel: each tile that fits timed on this cube, the fastest kept
+    tile, tile_ms = plan.autotune(cube, sigma, reps=3, stream=stream)
     ops, n_unique = alg_ops(cfg, plan)
     elem = 4 if args.dtype == "f32" else 2
     alg_bytes = cfg.n_pix * cfg.n_sub * cfg.n_t * elem + cfg.n_pix * 4 + cfg.n_pix * 16
@@ -871,7 +876,7 @@ def main():
                      "unit": "TFLOP/s", "frac": achieved / peak_ops,
                      "traffic": measured_traffic(cfg.ny, cfg.nx, args.dtype),
                      "kernel": search_kernel_name(cfg.n_t, args.dtype),
-                     "kernel_ms": kern_s * 1e3,
+                     "kernel_ms": kern_s * 1e3, "tile": tile, "tile_ms": tile_ms,
                      "ops_per_launch": ops, "peak_basis": f"{n_sm} SM x 128 FP32 lanes x "
                      f"{pk['sm_max_mhz']:.0f} MHz ({pk['source']} max clock)"},
         "hbm": {"achieved_gbs": hbm_gbs, "peak_gbs": pk["hbm_gbs"], "frac": hbm_gbs / pk["hbm_gbs"],

@@ -161,6 +161,38 @@ nsfrb_status nsfrb_full(nsfrb_plan_t plan, float *out_snr, int16_t *out_t_idx);
  * waits for the search.  ENOTREADY before the first search. */
 nsfrb_status nsfrb_last_timing(nsfrb_plan_t plan, float *search_ms, float *total_ms);
 
+/* ---- pixel x DM tile of the per-pixel search kernel ---------------------
+ * The search of Sec. 2.2 with KNOWN noise (and the FP32 slabs that MAD mode
+ * normalises into) runs a persistent kernel in which each CTA's 12 warps form
+ * `teams` teams, each team searching its own pixel with the DM row groups
+ * (unique delay rows) split among its warps, from `buffers` shared-memory
+ * copies of that pixel's rows (2 = the next pixel's copy overlaps this one's
+ * search).  A tile is coded 10 * teams + buffers; NSFRB_TILES lists the
+ * compiled ones.  Every tile gives the same candidates up to FP32 summation
+ * order (different warps build a row group's partial sums from scratch).
+ * Tile 0 = the first of 22, 21, 12 whose buffers fit in shared memory. */
+#define NSFRB_N_TILES 5
+#define NSFRB_TILES 12, 22, 21, 31, 41
+
+/* Preferred tile for rows stored as `dtype` (NSFRB_F32/BF16/F16; MAD-mode
+ * slabs are F32): 0 or one of NSFRB_TILES.  A tile whose buffers do not fit
+ * falls back to tile 0's order.  Errors: EINVAL (unknown dtype or tile). */
+nsfrb_status nsfrb_plan_set_tile(nsfrb_plan_t plan, int32_t dtype, int32_t tile);
+nsfrb_status nsfrb_plan_get_tile(nsfrb_plan_t plan, int32_t dtype, int32_t *tile);
+
+/* Time every tile that fits on the caller's cube (nsfrb_search arguments,
+ * no re-score), `reps` timed searches each after one warm-up, and keep the
+ * one with the smallest median search time as the plan's preference for the
+ * storage type the kernel searched.  h_tile (or NULL) gets that tile (0 when
+ * the plan's searches do not use this kernel: FULL output, MAD windows of
+ * n_t not a multiple of 4); h_ms[NSFRB_N_TILES] (or NULL) the medians in
+ * NSFRB_TILES order, -1 for tiles that do not fit.  Synchronous: it waits
+ * for every search it queues on `stream`.  Afterwards the plan's results are
+ * those of one search of the cube with the chosen tile.  Errors: as
+ * nsfrb_search; EINVAL for reps < 1. */
+nsfrb_status nsfrb_plan_autotune(nsfrb_plan_t plan, const void *d_cube, const float *d_sigma, int32_t reps,
+                                 void *stream, int32_t *h_tile, float *h_ms);
+
 /* ---- longer timescales (Sec. 2.2: the search is repeated on data binned by 5
  * samples (0.67 s, DM range x5 so that the same integer shifts apply) and by
  * 75 samples (10.05 s, no de-dispersion)) --------------------------------

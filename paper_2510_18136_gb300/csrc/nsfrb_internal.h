@@ -92,6 +92,8 @@ struct SearchParams {
     int32_t pipe;          // 1: barrier-free kernel (stage 1 or 3, KNOWN noise, records only)
     int32_t teams;         // barrier-free kernel: 1 (all warps on one pixel at a time) or 2 (two
                            // teams of half the warps, each on its own pixel with its own buffers)
+    int32_t nb;            // barrier-free kernel: pixel buffers per team, 2 (the pixel after next
+                           // copied while one is searched) or 1 (the next copied after a pixel)
     // ---- outputs (indexed by absolute pixel)
     PixRec *rec;
     float *full_snr;       // [pix][n_dm][n_w] or nullptr
@@ -115,7 +117,8 @@ __host__ __device__ inline SmemLayout smem_layout(const SearchParams &p, int C) 
     o += align_up(sizeof(int32_t) * ((size_t)p.n_u * kInfo + p.n_deltas + (size_t)p.n_u * p.n_sub), 16);
     L.xs = o;
     const int teams = (p.pipe && p.teams > 1) ? p.teams : 1;
-    const int nbuf = (p.stage == 1 || p.stage == 3) ? 2 * teams : 1;
+    const int nb = (p.pipe && p.nb == 1) ? 1 : 2;
+    const int nbuf = (p.stage == 1 || p.stage == 3) ? nb * teams : 1;
     const size_t es = (p.stage == 3) ? 2 : sizeof(float);
     o += align_up(es * (size_t)nbuf * p.n_sub * p.Tp, 128);
     L.stg = o;

@@ -106,7 +106,15 @@ void base_params(const nsfrb_plan_s *pl, SearchParams &sp) {
 
 // Choose the staging scheme for a cube pointer / row geometry and size the
 // shared memory (chunk size C, the device's per-block limit).  Returns false if nothing fits.
-bool choose_stage_for(int C, int max_smem, SearchParams &sp, size_t &smem) {
+// the compiled (teams, buffers per team) tiles of the barrier-free kernel, coded 10 * teams + buffers
+const int kTileCodes[NSFRB_N_TILES] = {NSFRB_TILES};
+bool tile_is_known(int t) {
+    for (const int k : kTileCodes)
+        if (k == t) return true;
+    return false;
+}
+
+bool choose_stage_for(int C, int max_smem, SearchParams &sp, size_t &smem, int tile_pref) {
     const uintptr_t base = reinterpret_cast<uintptr_t>(sp.cube);
     const int n_t = sp.n_t;
     const int epv = 16 / static_cast<int>(elem_size(sp.dtype));   // samples per 16 bytes
@@ -128,10 +136,14 @@ bool choose_stage_for(int C, int max_smem, SearchParams &sp, size_t &smem) {
             sp.stage = (sp.dtype == NSFRB_F32) ? 1 : 3;
             sp.stg_pitch = 0;
             sp.pipe = 1;
-            // two teams (each on its own pixel, half the row groups to build from scratch) where two
-            // double buffers fit, else one
-            for (int teams = 2; teams >= 1; --teams) {
-                sp.teams = teams;
+            // pixel x DM tile: the preferred one where it fits, else two teams (each on its own
+            // pixel, its share of the row groups to build from scratch) with two buffers each, then
+            // two teams of one buffer, then one team of two buffers
+            const int kTiles[4] = {tile_pref, 22, 21, 12};
+            for (const int t : kTiles) {
+                if (!tile_is_known(t)) continue;
+                sp.teams = t / 10;
+                sp.nb = t % 10;
                 const SmemLayout L = smem_layout(sp, C);
                 if (L.total <= static_cast<size_t>(max_smem)) {
                     smem = L.total;
@@ -140,6 +152,7 @@ bool choose_stage_for(int C, int max_smem, SearchParams &sp, size_t &smem) {
             }
         }
         sp.teams = 1;
+        sp.nb = 2;
     }
     sp.pipe = 0;
     int want = 0;
@@ -169,7 +182,13 @@ bool choose_stage_for(int C, int max_smem, SearchParams &sp, size_t &smem) {
 }
 
 bool choose_stage(const nsfrb_plan_s *pl, SearchParams &sp, size_t &smem) {
-    return choose_stage_for(pl->C, pl->max_smem, sp, smem);
+    return choose_stage_for(pl->C, pl->max_smem, sp, smem, pl->tile[sp.dtype]);
+}
+
+// records which tile the search launch of `sp` takes
+void note_tile(nsfrb_plan_s *pl, const SearchParams &sp) {
+    pl->last_tile = sp.pipe ? 10 * sp.teams + sp.nb : 0;
+    pl->last_tile_st = sp.dtype;
 }
 
 nsfrb_status ensure_device(nsfrb_plan_s *pl) {
@@ -251,6 +270,7 @@ nsfrb_status queue_search(nsfrb_plan_s *pl, const void *cube, int64_t cube_pix0,
     sp.new_blk = new_blk;
     size_t smem = 0;
     if (!choose_stage(pl, sp, smem)) return fail(pl, NSFRB_EINVAL, "shared memory does not fit this plan");
+    note_tile(pl, sp);
     const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(n, pl->n_sm)));
     return cuda_check(pl, launch_search(pl->C, sp, grid, smem, s), "search launch");
 }
@@ -301,6 +321,7 @@ nsfrb_status queue_search_mad(nsfrb_plan_s *pl, const void *cube, int dtype, int
         sp.n_items = m;
         size_t smem = 0;
         if (!choose_stage(pl, sp, smem)) return fail(pl, NSFRB_EINVAL, "shared memory does not fit this plan");
+        note_tile(pl, sp);
         const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(m, pl->n_sm)));
         if ((st = cuda_check(pl, launch_search(pl->C, sp, grid, smem, s), "search launch")) != NSFRB_OK) return st;
     }
@@ -669,6 +690,68 @@ nsfrb_status nsfrb_last_timing(nsfrb_plan_t plan, float *search_ms, float *total
     if (total_ms && (st = cuda_check(plan, cudaEventElapsedTime(total_ms, plan->t_start, plan->t_end), "elapsed")))
         return st;
     return NSFRB_OK;
+}
+
+nsfrb_status nsfrb_plan_set_tile(nsfrb_plan_t plan, int32_t dtype, int32_t tile) {
+    if (!plan) return fail(plan, NSFRB_EINVAL, "null plan");
+    if (dtype < NSFRB_F32 || dtype > NSFRB_F16) return fail(plan, NSFRB_EINVAL, "unknown storage type");
+    if (tile != 0 && !tile_is_known(tile)) return fail(plan, NSFRB_EINVAL, "unknown tile");
+    plan->tile[dtype] = tile;
+    return NSFRB_OK;
+}
+
+nsfrb_status nsfrb_plan_get_tile(nsfrb_plan_t plan, int32_t dtype, int32_t *tile) {
+    if (!plan || !tile) return fail(plan, NSFRB_EINVAL, "null argument");
+    if (dtype < NSFRB_F32 || dtype > NSFRB_F16) return fail(plan, NSFRB_EINVAL, "unknown storage type");
+    *tile = plan->tile[dtype];
+    return NSFRB_OK;
+}
+
+nsfrb_status nsfrb_plan_autotune(nsfrb_plan_t plan, const void *d_cube, const float *d_sigma, int32_t reps,
+                                 void *stream, int32_t *h_tile, float *h_ms) {
+    if (!plan || !d_cube || reps < 1) return fail(plan, NSFRB_EINVAL, "bad argument");
+    if (h_ms)
+        for (int k = 0; k < NSFRB_N_TILES; ++k) h_ms[k] = -1.0f;
+    // one untimed search finds the storage type the barrier-free kernel would search (the slabs of
+    // MAD mode are FP32) or that it does not apply
+    nsfrb_status st = nsfrb_search(plan, d_cube, d_sigma, nullptr, stream);
+    if (st == NSFRB_OK) st = nsfrb_last_timing(plan, nullptr, nullptr);
+    if (st != NSFRB_OK) return st;
+    const int s_t = plan->last_tile_st;
+    if (plan->last_tile == 0 || s_t < 0) {
+        if (h_tile) *h_tile = 0;
+        return NSFRB_OK;
+    }
+    const int32_t keep = plan->tile[s_t];
+    int32_t best = 0;
+    float best_ms = 0.0f;
+    std::vector<float> t(reps);
+    for (int k = 0; k < NSFRB_N_TILES; ++k) {
+        plan->tile[s_t] = kTileCodes[k];
+        for (int r = -1; r < reps; ++r) {   // one warm-up search per tile
+            st = nsfrb_search(plan, d_cube, d_sigma, nullptr, stream);
+            if (st == NSFRB_OK) st = nsfrb_last_timing(plan, r >= 0 ? &t[r] : nullptr, nullptr);
+            if (st != NSFRB_OK) {
+                plan->tile[s_t] = keep;
+                return st;
+            }
+            if (plan->last_tile != kTileCodes[k]) break;   // does not fit: another tile ran
+        }
+        if (plan->last_tile != kTileCodes[k]) continue;
+        std::sort(t.begin(), t.end());
+        const float med = t[reps / 2];
+        if (h_ms) h_ms[k] = med;
+        if (best == 0 || med < best_ms) {
+            best = kTileCodes[k];
+            best_ms = med;
+        }
+    }
+    plan->tile[s_t] = best ? best : keep;
+    if (h_tile) *h_tile = plan->tile[s_t];
+    // the plan's results are those of a search with the chosen tile
+    st = nsfrb_search(plan, d_cube, d_sigma, nullptr, stream);
+    if (st == NSFRB_OK) st = nsfrb_last_timing(plan, nullptr, nullptr);
+    return st;
 }
 
 void nsfrb_destroy(nsfrb_plan_t plan) {

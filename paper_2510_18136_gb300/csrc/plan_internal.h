@@ -23,6 +23,10 @@ struct nsfrb_plan_s {
     int n_u = 0, n_u_active = 0, n_deltas = 0;
     int C = 0, Tp = 0;
     int32_t wclass[nsfrb::kMaxW] = {};
+    // barrier-free kernel pixel x DM tile (10 * teams + buffers per team) per storage type of the
+    // searched rows (FP32, BF16, FP16); 0 = the first of the default order that fits
+    int32_t tile[3] = {0, 0, 0};
+    int32_t last_tile = 0, last_tile_st = -1;   // tile and storage type of the last search launch
 
     // device state (allocated on first use)
     bool dev_ready = false;
@@ -83,7 +87,7 @@ size_t elem_size(int dtype);
 void destroy_stream_state(nsfrb_plan_s *pl);
 void base_params(const nsfrb_plan_s *pl, SearchParams &sp);
 bool choose_stage(const nsfrb_plan_s *pl, SearchParams &sp, size_t &smem);
-bool choose_stage_for(int C, int max_smem, SearchParams &sp, size_t &smem);
+bool choose_stage_for(int C, int max_smem, SearchParams &sp, size_t &smem, int tile_pref = 0);
 
 cudaError_t launch_search_c1(const SearchParams &, int, size_t, cudaStream_t);
 cudaError_t launch_search_c3(const SearchParams &, int, size_t, cudaStream_t);

@@ -3,4 +3,5 @@
 
 namespace nsfrb {
 NSFRB_INSTANTIATE_SEARCH(1)
+NSFRB_INSTANTIATE_PIPE(1, 0)
 }  // namespace nsfrb

@@ -3,4 +3,5 @@
 
 namespace nsfrb {
 NSFRB_INSTANTIATE_SEARCH(17)
+NSFRB_INSTANTIATE_PIPE(17, 0)
 }  // namespace nsfrb

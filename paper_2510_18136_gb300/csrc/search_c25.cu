@@ -3,4 +3,5 @@
 
 namespace nsfrb {
 NSFRB_INSTANTIATE_SEARCH(25)
+NSFRB_INSTANTIATE_PIPE(25, 0)
 }  // namespace nsfrb

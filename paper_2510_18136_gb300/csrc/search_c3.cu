@@ -3,4 +3,5 @@
 
 namespace nsfrb {
 NSFRB_INSTANTIATE_SEARCH(3)
+NSFRB_INSTANTIATE_PIPE(3, 0)
 }  // namespace nsfrb

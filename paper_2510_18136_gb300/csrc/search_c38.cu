@@ -4,4 +4,5 @@
 
 namespace nsfrb {
 NSFRB_INSTANTIATE_SEARCH(38)
+NSFRB_INSTANTIATE_PIPE(38, 0)
 }  // namespace nsfrb

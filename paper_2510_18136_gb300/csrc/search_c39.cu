@@ -3,4 +3,5 @@
 
 namespace nsfrb {
 NSFRB_INSTANTIATE_SEARCH(39)
+NSFRB_INSTANTIATE_PIPE(39, 0)
 }  // namespace nsfrb

@@ -3,4 +3,5 @@
 
 namespace nsfrb {
 NSFRB_INSTANTIATE_SEARCH(5)
+NSFRB_INSTANTIATE_PIPE(5, 0)
 }  // namespace nsfrb

@@ -3,4 +3,5 @@
 
 namespace nsfrb {
 NSFRB_INSTANTIATE_SEARCH(9)
+NSFRB_INSTANTIATE_PIPE(9, 0)
 }  // namespace nsfrb

@@ -1246,12 +1246,15 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel(const __grid_consta
 // counts itself done; the last warp of a pixel combines the groups in row order (the DM tie rule),
 // writes the pixel's record, and starts the copy of the team's pixel two ahead into the buffer it
 // frees (with that pixel's 1 / (sigma sqrt(w))).  Warps of a team drift apart by at most one pixel.
+// With NB = 1 buffer per team the copy of the team's next pixel starts only when a pixel is done
+// (the team waits for it, the other team keeps the SM busy): for tiles too large for two buffers
+// per team.
 // ST is the storage type of the rows, kept as they are in shared memory: FP32, or BF16 / FP16 read
 // in place by the mixed-precision adds (no widening pass).  A window that starts at any sample t_off
 // is copied from the 16-byte boundary below it and read from element eoff = t_off mod (16 / size)
 // of the staged row; when the copy then carries samples past the window, the de-dispersed samples
 // past the valid range are set to -inf instead of relying on -inf past the window.
-template <int C, int ST, int TEAMS>
+template <int C, int ST, int TEAMS, int NB>
 __global__ void __launch_bounds__(kThreads, 1) search_kernel_pipe(const __grid_constant__ SearchParams p) {
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr int kEs = (ST == 0) ? 4 : 2;          // bytes per stored sample
@@ -1283,7 +1286,7 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel_pipe(const __grid_c
     const int32_t *s_delta = s_table + p.n_u * kInfo;
     const int32_t *s_shift = s_delta + p.n_deltas;
     // -inf past the copied part of every row of every buffer (never overwritten)
-    for (int b = 0; b < 2 * TEAMS; ++b)
+    for (int b = 0; b < NB * TEAMS; ++b)
         for (int i = tid; i < n_sub * (Tp - row_elems); i += kThreads) {
             const int k = i / (Tp - row_elems), t = row_elems + i % (Tp - row_elems);
             unsigned char *row = s_xs + b * buf_bytes + (size_t)k * Tp * kEs;
@@ -1299,7 +1302,7 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel_pipe(const __grid_c
         return p.pix_list ? static_cast<int64_t>(p.pix_list[it]) : p.pix0 + it;
     };
     // slot (team, b): buffer, barrier, records, 1 / (sigma sqrt(w)) and done counter of one pixel
-    const int slot0 = 2 * team;
+    const int slot0 = NB * team;
     // one warp: 1 / (sigma sqrt(w)) of item `it` into slot s, then its rows into buffer s
     // (lane 0 arms the barrier, lane k copies subband k)
     auto issue_warp = [&](int64_t it, int sl) {
@@ -1320,7 +1323,7 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel_pipe(const __grid_c
                      &s_bar[sl]);
     };
     if (tid == 0) {
-        for (int sl = 0; sl < 2 * TEAMS; ++sl) {
+        for (int sl = 0; sl < NB * TEAMS; ++sl) {
             mbar_init(&s_bar[sl], 1);
             s_cnt[sl] = 0;
         }
@@ -1334,7 +1337,7 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel_pipe(const __grid_c
     const int64_t it0 = static_cast<int64_t>(blockIdx.x) * TEAMS + team;
     if (wt == 0) {
         if (it0 < n_items) issue_warp(it0, slot0);
-        if (it0 + G < n_items) issue_warp(it0 + G, slot0 + 1);
+        if (NB == 2 && it0 + G < n_items) issue_warp(it0 + G, slot0 + 1);
     }
 
     const int n_ua = p.n_u_active;
@@ -1342,9 +1345,9 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel_pipe(const __grid_c
     int issued_last = -1;   // local index of the last item whose copy this warp started
     int i = 0;
     for (int64_t it = it0; it < n_items; it += G, ++i) {
-        const int b = i & 1, sl = slot0 + b;
+        const int b = i % NB, sl = slot0 + b;
         if (*reinterpret_cast<volatile int32_t *>(s_flag)) break;
-        if (!mbar_wait(&s_bar[sl], static_cast<uint32_t>(i >> 1) & 1u)) {
+        if (!mbar_wait(&s_bar[sl], static_cast<uint32_t>(i / NB) & 1u)) {
             if (lane == 0) {
                 atomicOr(s_flag, ERR_WAIT_TIMEOUT);
                 atomicOr(p.err, ERR_WAIT_TIMEOUT);
@@ -1382,57 +1385,77 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel_pipe(const __grid_c
                 s_cnt[sl] = 0;
             }
             __syncwarp();
-            const int64_t nxt = it + 2 * G;
+            const int64_t nxt = it + NB * G;
             if (nxt < n_items) {
                 issue_warp(nxt, sl);
-                issued_last = i + 2;
+                issued_last = i + NB;
             }
         }
         __syncwarp();
     }
     // after an error: wait (bounded) for copies this warp started that may still be in flight
     if (*reinterpret_cast<volatile int32_t *>(s_flag) && lane == 0 && issued_last >= 0)
-        mbar_wait(&s_bar[slot0 + (issued_last & 1)], static_cast<uint32_t>(issued_last >> 1) & 1u);
+        mbar_wait(&s_bar[slot0 + issued_last % NB], static_cast<uint32_t>(issued_last / NB) & 1u);
 }
 
 }  // namespace dev
 
-// 16-bit rows read in place need the sample-pair path (even chunks); odd chunks get FP32 only.
-#define NSFRB_PIPE_LAUNCH(CC, ST)                                                              \
-    do {                                                                                       \
-        if (p.teams == 2)                                                                      \
-            dev::search_kernel_pipe<CC, ST, 2><<<grid, kThreads, smem, s>>>(p);                \
-        else                                                                                   \
-            dev::search_kernel_pipe<CC, ST, 1><<<grid, kThreads, smem, s>>>(p);                \
-    } while (0)
-#define NSFRB_PIPE_ATTR(CC, ST)                                                                \
-    do {                                                                                       \
-        if (e == cudaSuccess)                                                                  \
-            e = cudaFuncSetAttribute(dev::search_kernel_pipe<CC, ST, 1>,                       \
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, sm);         \
-        if (e == cudaSuccess)                                                                  \
-            e = cudaFuncSetAttribute(dev::search_kernel_pipe<CC, ST, 2>,                       \
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, sm);         \
-    } while (0)
+// The barrier-free kernel's pixel x DM tiles (teams, buffers per team), one launcher per chunk size
+// and storage type (16-bit rows read in place need the sample-pair path of even chunks).
+#define NSFRB_PIPE_CASE(CC, ST, T, B)                                                          \
+    case 10 * T + B:                                                                           \
+        dev::search_kernel_pipe<CC, ST, T, B><<<grid, kThreads, smem, s>>>(p);                 \
+        break;
+#define NSFRB_PIPE_ATTR1(CC, ST, T, B)                                                         \
+    if (e == cudaSuccess)                                                                      \
+        e = cudaFuncSetAttribute(dev::search_kernel_pipe<CC, ST, T, B>,                        \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+#define NSFRB_INSTANTIATE_PIPE(CC, ST)                                                         \
+    cudaError_t launch_pipe_c##CC##_s##ST(const SearchParams &p, int grid, size_t smem, cudaStream_t s) { \
+        switch (10 * p.teams + p.nb) {                                                         \
+            NSFRB_PIPE_CASE(CC, ST, 1, 2)                                                      \
+            NSFRB_PIPE_CASE(CC, ST, 2, 2)                                                      \
+            NSFRB_PIPE_CASE(CC, ST, 2, 1)                                                      \
+            NSFRB_PIPE_CASE(CC, ST, 3, 1)                                                      \
+            NSFRB_PIPE_CASE(CC, ST, 4, 1)                                                      \
+            default:                                                                           \
+                return cudaErrorInvalidValue;                                                  \
+        }                                                                                      \
+        return cudaGetLastError();                                                             \
+    }                                                                                          \
+    cudaError_t prepare_pipe_c##CC##_s##ST(size_t smem) {                                      \
+        const int sm = static_cast<int>(smem);                                                 \
+        cudaError_t e = cudaSuccess;                                                           \
+        NSFRB_PIPE_ATTR1(CC, ST, 1, 2)                                                         \
+        NSFRB_PIPE_ATTR1(CC, ST, 2, 2)                                                         \
+        NSFRB_PIPE_ATTR1(CC, ST, 2, 1)                                                         \
+        NSFRB_PIPE_ATTR1(CC, ST, 3, 1)                                                         \
+        NSFRB_PIPE_ATTR1(CC, ST, 4, 1)                                                         \
+        return e;                                                                              \
+    }
+
+// The barrier kernels of a chunk size and its launch dispatch; the barrier-free kernel's launchers
+// come from NSFRB_INSTANTIATE_PIPE (16-bit ones in translation units of their own).
 #define NSFRB_INSTANTIATE_SEARCH(CC)                                                           \
+    cudaError_t launch_pipe_c##CC##_s0(const SearchParams &, int, size_t, cudaStream_t);      \
+    cudaError_t launch_pipe_c##CC##_s1(const SearchParams &, int, size_t, cudaStream_t);      \
+    cudaError_t launch_pipe_c##CC##_s2(const SearchParams &, int, size_t, cudaStream_t);      \
+    cudaError_t prepare_pipe_c##CC##_s0(size_t);                                               \
+    cudaError_t prepare_pipe_c##CC##_s1(size_t);                                               \
+    cudaError_t prepare_pipe_c##CC##_s2(size_t);                                               \
     cudaError_t launch_search_c##CC(const SearchParams &p, int grid, size_t smem, cudaStream_t s) { \
         if (p.pipe) {                                                                          \
+            if (p.dtype == 0) return launch_pipe_c##CC##_s0(p, grid, smem, s);                 \
             if constexpr (CC % 2 == 0) {                                                       \
-                if (p.dtype == 1)                                                              \
-                    NSFRB_PIPE_LAUNCH(CC, 1);                                                  \
-                else if (p.dtype == 2)                                                         \
-                    NSFRB_PIPE_LAUNCH(CC, 2);                                                  \
-                else                                                                           \
-                    NSFRB_PIPE_LAUNCH(CC, 0);                                                  \
-            } else {                                                                           \
-                if (p.dtype != 0) return cudaErrorInvalidValue;                                \
-                NSFRB_PIPE_LAUNCH(CC, 0);                                                      \
+                if (p.dtype == 1) return launch_pipe_c##CC##_s1(p, grid, smem, s);             \
+                return launch_pipe_c##CC##_s2(p, grid, smem, s);                               \
             }                                                                                  \
-        } else if (p.full_snr) {                                                               \
-            dev::search_kernel<CC, true><<<grid, kThreads, smem, s>>>(p);                      \
-        } else {                                                                               \
-            dev::search_kernel<CC, false><<<grid, kThreads, smem, s>>>(p);                     \
+            return cudaErrorInvalidValue;                                                      \
         }                                                                                      \
+        if (p.full_snr)                                                                        \
+            dev::search_kernel<CC, true><<<grid, kThreads, smem, s>>>(p);                      \
+        else                                                                                   \
+            dev::search_kernel<CC, false><<<grid, kThreads, smem, s>>>(p);                     \
         return cudaGetLastError();                                                             \
     }                                                                                          \
     cudaError_t prepare_search_c##CC(size_t smem) {                                            \
@@ -1442,10 +1465,10 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel_pipe(const __grid_c
         if (e == cudaSuccess)                                                                  \
             e = cudaFuncSetAttribute(dev::search_kernel<CC, true>,                             \
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, sm);         \
-        NSFRB_PIPE_ATTR(CC, 0);                                                                \
+        if (e == cudaSuccess) e = prepare_pipe_c##CC##_s0(smem);                               \
         if constexpr (CC % 2 == 0) {                                                           \
-            NSFRB_PIPE_ATTR(CC, 1);                                                            \
-            NSFRB_PIPE_ATTR(CC, 2);                                                            \
+            if (e == cudaSuccess) e = prepare_pipe_c##CC##_s1(smem);                           \
+            if (e == cudaSuccess) e = prepare_pipe_c##CC##_s2(smem);                           \
         }                                                                                      \
         return e;                                                                              \
     }

@@ -24,6 +24,9 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ETRUNC, ENOTREADY = range(7)
 
 _DTYPES = {"f32": F32, "bf16": BF16, "f16": F16}
 _TORCH = {F32: torch.float32, BF16: torch.bfloat16, F16: torch.float16}
+# pixel x DM tiles of the search kernel, 10 * teams + buffers per team (NSFRB_TILES)
+TILES = (12, 22, 21, 31, 41)
+N_TILES = len(TILES)
 
 
 class nsfrb_config(ctypes.Structure):
@@ -79,6 +82,9 @@ def _load() -> ctypes.CDLL:
         "nsfrb_best": ([P, P, P], c_int32),
         "nsfrb_full": ([P, P, P], c_int32),
         "nsfrb_last_timing": ([P, POINTER(c_float), POINTER(c_float)], c_int32),
+        "nsfrb_plan_set_tile": ([P, c_int32, c_int32], c_int32),
+        "nsfrb_plan_get_tile": ([P, c_int32, POINTER(c_int32)], c_int32),
+        "nsfrb_plan_autotune": ([P, P, P, c_int32, P, POINTER(c_int32), POINTER(c_float)], c_int32),
         "nsfrb_search_static": ([P, P, P, P, c_int32, P, P], c_int32),
         "nsfrb_stream_open": ([P, c_int32, c_size_t], c_int32),
         "nsfrb_stream_bytes": ([P, c_int32, POINTER(c_size_t)], c_int32),
@@ -255,6 +261,27 @@ class Plan:
         a, b = c_float(), c_float()
         _check(lib.nsfrb_last_timing(self._h, ctypes.byref(a), ctypes.byref(b)), "nsfrb_last_timing")
         return float(a.value), float(b.value)
+
+    # ------------------------------------------------------------------ kernel tile
+    def set_tile(self, dtype: int, tile: int) -> None:
+        """``nsfrb_plan_set_tile``: preferred (10 * teams + buffers) tile for rows stored as dtype."""
+        _check(lib.nsfrb_plan_set_tile(self._h, int(dtype), int(tile)), "nsfrb_plan_set_tile")
+
+    def get_tile(self, dtype: int) -> int:
+        t = c_int32()
+        _check(lib.nsfrb_plan_get_tile(self._h, int(dtype), ctypes.byref(t)), "nsfrb_plan_get_tile")
+        return int(t.value)
+
+    def autotune(self, cube: torch.Tensor, sigma: torch.Tensor | None = None, reps: int = 3, stream=None):
+        """``nsfrb_plan_autotune``: (chosen tile, {tile: median search ms} of the tiles that fit)."""
+        self._check_cube(cube, self.dtype, "cuda")
+        if sigma is not None:
+            assert sigma.is_cuda and sigma.dtype == torch.float32 and sigma.numel() == self.cfg.n_pix
+        tile = c_int32()
+        ms = (c_float * N_TILES)()
+        _check(lib.nsfrb_plan_autotune(self._h, _ptr(cube), _ptr(sigma), int(reps), _stream_handle(stream),
+                                       ctypes.byref(tile), ms), "nsfrb_plan_autotune")
+        return int(tile.value), {t: float(m) for t, m in zip(TILES, ms) if m >= 0}
 
     # ------------------------------------------------------------------ serving
     def stream_bytes(self, n_blk: int) -> int:

@@ -93,3 +93,19 @@ def test_search_without_results_is_not_ready(native):
     with pytest.raises(native.NsfrbError) as e:
         plan.candidates()
     assert e.value.status == native.ENOTREADY
+
+
+def test_tile_codes_and_preference(native):
+    """The binding's tile list is the header's; the preference is host state, validated."""
+    txt = open(os.path.join(ROOT, "include", "nsfrb.h")).read()
+    codes = tuple(int(x) for x in re.search(r"#define NSFRB_TILES ([\d, ]+)", txt).group(1).split(","))
+    assert codes == native.TILES
+    assert int(re.search(r"#define NSFRB_N_TILES (\d+)", txt).group(1)) == native.N_TILES
+    plan = native.Plan(synth.config_small())
+    assert plan.get_tile(native.F32) == 0
+    plan.set_tile(native.BF16, 41)
+    assert plan.get_tile(native.BF16) == 41 and plan.get_tile(native.F32) == 0
+    for dtype, tile in ((native.F32, 23), (native.F32, 11), (3, 12)):
+        with pytest.raises(native.NsfrbError) as e:
+            plan.set_tile(dtype, tile)
+        assert e.value.status == native.EINVAL

@@ -313,3 +313,48 @@ def test_records_mode_mad_order_statistics(native, kind):
     assert bad == 0
     parity.compare_best(snr, idx, best)
     parity.compare_candidates(cand, best, cfg.threshold, np.arange(cfg.n_pix), cfg.nx)
+
+
+# ----------------------------------------------------------------------------- pixel x DM tiles
+
+@pytest.mark.parametrize("dtype,noise,n_t", [("f32", "known", 1200), ("f32", "known", 640),
+                                             ("bf16", "known", 1200), ("f16", "known", 1000),
+                                             ("bf16", "mad", 840)])
+def test_every_tile_matches_oracle(native, dtype, noise, n_t):
+    """Every (teams, buffers) tile of the barrier-free kernel that fits gives the oracle's per-pixel
+    records and candidates; the autotuner keeps the fastest of them and leaves the plan's results
+    those of that tile."""
+    rng = np.random.default_rng(n_t + 7 * len(dtype))
+    tdt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[dtype]
+    if noise == "mad":
+        cfg = synth.config_stress(7, 9, n_t=n_t)
+        cfg.widths = np.array([w for w in cfg.widths if w <= n_t], np.int32)
+        cube = synth.beam_student_noise(cfg, 3, dtype=torch.float32).to(tdt)
+        sig = None
+    else:
+        widths = [1, 2, 3, 4, 8, 16, 32, 64, 128, 256, 512]
+        cfg = synth.SearchConfig(ny=7, nx=11, n_t=n_t, dm=np.sort(rng.uniform(0, 2500, 41)),
+                                 widths=np.array(widths, np.int32), threshold=4.5)
+        cube = _psf_cube(cfg, n_t, 6, dm_range=(0.0, 2500.0)).to(tdt)
+        sig = rng.uniform(4.0, 8.0, cfg.n_pix).astype(np.float32)
+    dev = cube.cuda()
+    sg = None if sig is None else torch.as_tensor(sig).cuda()
+    tab, res, best, bad = _oracle(cfg, cube.float().numpy(), sigma=sig, mad=(noise == "mad"))
+    assert bad == 0
+    plan = native.Plan(cfg, dtype=dtype, noise=noise, out="candidates")
+    chosen, ms = plan.autotune(dev, sg, reps=2)
+    st = native.F32 if noise == "mad" else plan.dtype      # MAD slabs are searched as FP32
+    assert chosen in ms and ms[chosen] == min(ms.values()) and plan.get_tile(st) == chosen
+    assert 12 in ms and len(ms) >= 2                       # one team of two buffers always fits
+    checked = []
+    for tile in [chosen] + [t for t in ms if t != chosen]:
+        if tile != chosen:
+            plan.set_tile(st, tile)
+            plan.search(dev, sg)
+        cand = plan.candidates()
+        snr, idx = plan.best()
+        parity.compare_best(snr, idx, best)
+        parity.compare_candidates(cand, best, cfg.threshold, np.arange(cfg.n_pix), cfg.nx)
+        checked.append(tile)
+    plan.close()
+    assert sorted(checked) == sorted(ms)
