@@ -49,8 +49,8 @@ typedef enum {
 /* Storage type of the input cube.  Arithmetic is always FP32. */
 enum { NSFRB_F32 = 0, NSFRB_BF16 = 1, NSFRB_F16 = 2 };
 
-/* Noise model (Sec. 2.2: "median subtracted in each pixel ... normalized by
- * the running standard deviation").
+/* Noise model (Sec. 2.2: each pixel's median is removed and the samples are
+ * scaled by a running noise estimate).
  * KNOWN: the caller supplies sigma_D(p), the noise of the de-dispersed
  *        series of pixel p (d_sigma), or NULL for sqrt(n_sub) (unit noise
  *        per subband); no median subtraction.

@@ -45,6 +45,15 @@ nsfrb_status nsfrb_dbg_conv3(int32_t path, int32_t B, int32_t D, int32_t H, int3
  * if it did not, EINVAL for a bad limit.  Synchronous. */
 nsfrb_status nsfrb_dbg_wait_timeout(int32_t limit_ms);
 
+/* The MAD normalisation pass of the search (Sec. 2.2, robust reading) on its own, asynchronous on
+ * `stream`: for each of the n_rows rows of n_t samples of d_in (`dtype` storage, row-major),
+ *   m = median, MAD = median |x - m| (exact order statistics; for even n_t the mean of the two
+ *   middle values, formed in FP32), y = (x - m) * (1 / (1.4826 MAD)) in FP32,
+ * into d_out [n_rows][n_t] FP32; a row with MAD 0 is written as zeros and sets d_bad[row] = 1
+ * (d_bad: n_rows bytes, zeroed here first).  n_t in [1, 1247].  EINVAL for other sizes. */
+nsfrb_status nsfrb_dbg_mad_normalise(const void *d_in, int32_t dtype, int64_t n_rows, int32_t n_t, float *d_out,
+                                     uint8_t *d_bad, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -74,9 +74,9 @@ static double median_of(const double *v, int n, double *work)
 }
 
 /*
- * Robust per-(pixel, subband) normalisation over the time window (Sec. 2.2:
- * "median subtracted in each pixel", "normalized by the running standard
- * deviation"; the robust reading uses the median absolute deviation):
+ * Robust per-(pixel, subband) normalisation over the time window (Sec. 2.2
+ * removes each pixel's median and scales by a running noise estimate; the
+ * robust reading takes the median absolute deviation as that estimate):
  *   m   = median_t x[t]
  *   MAD = median_t |x[t] - m|
  *   y[t] = (x[t] - m) / (1.4826 * MAD)

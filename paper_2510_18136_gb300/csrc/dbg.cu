@@ -41,3 +41,19 @@ extern "C" nsfrb_status nsfrb_dbg_wait_timeout(int32_t limit_ms) {
     if (e != cudaSuccess) return NSFRB_ECUDA;
     return (h_err & ERR_WAIT_TIMEOUT) ? NSFRB_ETIMEOUT : NSFRB_OK;
 }
+
+extern "C" nsfrb_status nsfrb_dbg_mad_normalise(const void *d_in, int32_t dtype, int64_t n_rows, int32_t n_t,
+                                                float *d_out, uint8_t *d_bad, void *stream) {
+    using namespace nsfrb;
+    if (!d_in || !d_out || !d_bad || n_rows < 1 || n_t < 1 || n_t > kMaxT || dtype < NSFRB_F32 || dtype > NSFRB_F16)
+        return NSFRB_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int dev = 0, n_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return NSFRB_ECUDA;
+    // rows as pixels of one subband: bad[] is then per row
+    if (cudaMemsetAsync(d_bad, 0, static_cast<size_t>(n_rows), s) != cudaSuccess) return NSFRB_ECUDA;
+    if (launch_mad_normalise(d_in, dtype, 0, n_rows, 1, n_t, d_out, d_bad, n_sm, s) != cudaSuccess) return NSFRB_ECUDA;
+    return NSFRB_OK;
+}

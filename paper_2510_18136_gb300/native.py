@@ -119,6 +119,7 @@ def _load() -> ctypes.CDLL:
         "nsfrb_dbg_conv3": ([c_int32, c_int32, c_int32, c_int32, c_int32, c_int32, c_int32, P, P, P, P, P, P, P],
                             c_int32),
         "nsfrb_dbg_wait_timeout": ([c_int32], c_int32),
+        "nsfrb_dbg_mad_normalise": ([P, c_int32, c_int64, c_int32, P, P, P], c_int32),
         "nsfrb_destroy": ([P], None),
         "nsfrb_strerror": ([c_int32], ctypes.c_char_p),
         "nsfrb_last_error": ([], ctypes.c_char_p),
