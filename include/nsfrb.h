@@ -170,7 +170,8 @@ nsfrb_status nsfrb_last_timing(nsfrb_plan_t plan, float *search_ms, float *total
  * search).  A tile is coded 10 * teams + buffers; NSFRB_TILES lists the
  * compiled ones.  Every tile gives the same candidates up to FP32 summation
  * order (different warps build a row group's partial sums from scratch).
- * Tile 0 = the first of 22, 21, 12 whose buffers fit in shared memory. */
+ * Tile 0 = the first of 41, 31, 22, 21, 12 whose buffers fit in shared
+ * memory (16-bit rows of a full window: 41; FP32 rows: 21). */
 #define NSFRB_N_TILES 5
 #define NSFRB_TILES 12, 22, 21, 31, 41
 

@@ -136,10 +136,11 @@ bool choose_stage_for(int C, int max_smem, SearchParams &sp, size_t &smem, int t
             sp.stage = (sp.dtype == NSFRB_F32) ? 1 : 3;
             sp.stg_pitch = 0;
             sp.pipe = 1;
-            // pixel x DM tile: the preferred one where it fits, else two teams (each on its own
-            // pixel, its share of the row groups to build from scratch) with two buffers each, then
-            // two teams of one buffer, then one team of two buffers
-            const int kTiles[4] = {tile_pref, 22, 21, 12};
+            // pixel x DM tile: the preferred one where it fits, else the most teams that fit (each
+            // team on its own pixel, fewer row groups per pixel to build from scratch and more rows
+            // per warp between pixel changes): four, three or two teams of one buffer (two teams of
+            // two buffers before two of one), then one team of two buffers
+            const int kTiles[6] = {tile_pref, 41, 31, 22, 21, 12};
             for (const int t : kTiles) {
                 if (!tile_is_known(t)) continue;
                 sp.teams = t / 10;
