@@ -64,6 +64,11 @@ def parse():
                     help="timed launches of the imager section, one 25-sample block each (0: skip)")
     ap.add_argument("--stress-steps", type=int, default=5,
                     help="timed searches of the 512x512 BF16 MAD stress workload (0: skip)")
+    ap.add_argument("--stress-size", type=int, default=512,
+                    help="side of the stress image (512 is the stress workload; smaller for profiling)")
+    ap.add_argument("--serving-fields", default="301x301,257x257,193x193,129x129",
+                    help="comma-separated field grids of the serving section (the four fields are the "
+                         "serving workload; smaller for profiling)")
     ap.add_argument("--seed", type=int, default=0)
     return ap.parse_args()
 
@@ -105,8 +110,9 @@ def make_cube(native, synth, cfg, seed, device, dtype):
 
 
 # DRAM bytes (read + write) per 301x301 FP32 launch from an ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum, scaled from a 64x64 launch), valid for the kernel source with this sha256 prefix.
-NCU_TRAFFIC = {"sha256_16": "7c155e588df33d0d", "bytes": 7.030e9, "workload": (301, 301, "f32")}
+# dram__bytes_write.sum of a 128x128 launch, 1262.3 MB, scaled by 90601 / 16384 pixels), valid for the
+# kernel source with this sha256 prefix.
+NCU_TRAFFIC = {"sha256_16": "aa3ae44410ca656c", "bytes": 6.980e9, "workload": (301, 301, "f32")}
 
 
 # DRAM bytes of one imager call (grid_kernel + transform_kernel) from the ncu launch list of the
@@ -133,15 +139,19 @@ def measured_traffic(ny, nx, dtype):
     return NCU_TRAFFIC["bytes"]
 
 
-def search_kernel_name(n_t, dtype, noise="known"):
-    """The kernel the library launches for this window: chunks of C samples per lane, the smallest
+def search_kernel_name(n_t, dtype, noise="known", tile=None):
+    """The kernels the library launches for this window: chunks of C samples per lane, the smallest
     compiled C with 32 C > n_t.  With known noise the barrier-free kernel runs (FP32 rows; 16-bit
-    rows read in place when C is even and the rows fill whole 16-byte units); MAD normalisation
-    runs the staged kernel with per-pixel barriers."""
+    rows read in place when C is even and the rows fill whole 16-byte units), with the pixel x DM
+    tile (teams, buffers per team) the plan chose; MAD normalisation is a pass of its own into FP32
+    slabs that the barrier-free kernel then searches."""
     c = next(c for c in (1, 3, 5, 9, 17, 25, 38, 39) if 32 * c >= n_t + 1)
     st = {"f32": 0, "bf16": 1, "f16": 2}[dtype]
-    if noise == "known" and (st == 0 or (c % 2 == 0 and n_t % 8 == 0)):
-        return f"search_kernel_pipe<{c}, {st}>"
+    tt = "" if tile is None else f", {int(tile) // 10}, {int(tile) % 10}"
+    if noise == "mad":
+        return f"mad_normalise_kernel + search_kernel_pipe<{c}, 0{tt}> (FP32 slabs)"
+    if st == 0 or (c % 2 == 0 and n_t % 8 == 0):
+        return f"search_kernel_pipe<{c}, {st}{tt}>"
     return f"search_kernel<{c}, false>"
 
 
@@ -345,7 +355,7 @@ def serving_latency(native, synth, n_blocks: int, paced_blocks: int, seed: int =
         return np.array(lat), time.perf_counter() - t0
 
     lat, wall = run(n_blocks, False)
-    lat = lat[8:]                                   # the first two blocks of each field are warm-up
+    lat = lat[2 * len(fields):]                     # the first two blocks of each field are warm-up
     out = {"fields": [f"{ny}x{nx}" for ny, nx in SERVING_FIELDS], "storage": "bf16",
            "rescore_eps": SERVING_EPS, "rescore_from": "pinned host FP32 window", "block_samples": 25,
            "window_samples": 1200, "blocks_per_field": n_blocks, "paced": False,
@@ -658,16 +668,17 @@ def imager_section(native, steps: int, seed: int = 0):
                              "sample": f"{len(pairs)} images of the block, FP64 numpy"}}
 
 
-def stress_section(native, synth, steps: int, seed: int = 0):
+def stress_section(native, synth, steps: int, seed: int = 0, size: int = 512):
     """The stress workload: 512x512 px x 16 sub x 1200 samples stored in BF16, beam-scaled
     Student-t noise, MAD normalisation per (pixel, subband), 500 injections, 256 DM 0-4000,
     12 widths; search kernel time by CUDA events, ALU roofline on the definition's operations
     (the MAD normalisation's own work is not counted)."""
     import torch
     import oracle
-    cfg = synth.config_stress()
+    cfg = synth.config_stress(size, size)
     cube = synth.beam_student_noise(cfg, seed + 5, device="cuda", dtype=torch.float32)
-    raw = synth.draw_injections(cfg, 500, seed + 6, dm_range=(0.0, 4000.0), max_width=cfg.n_t)
+    n_inj = max(8, round(500 * cfg.n_pix / (512 * 512)))    # 500 on the 512x512 image
+    raw = synth.draw_injections(cfg, n_inj, seed + 6, dm_range=(0.0, 4000.0), max_width=cfg.n_t)
     sh = oracle.delay_table(cfg.freq_mhz, raw["dm"])
     inj = synth.place_injections(raw, sh, cfg.n_t, cfg.n_sub,
                                  synth.beam_sigma(cfg)[raw["row"] * cfg.nx + raw["col"]])
@@ -720,7 +731,7 @@ def stress_section(native, synth, steps: int, seed: int = 0):
     del cube
     torch.cuda.empty_cache()
     return {"workload": f"{cfg.ny}x{cfg.nx} px x {cfg.n_sub} sub x {cfg.n_t} samples BF16, MAD normalisation, "
-                        f"{len(cfg.dm)} DM 0-4000 ({n_unique} distinct rows), {len(cfg.widths)} widths, 500 injections",
+                        f"{len(cfg.dm)} DM 0-4000 ({n_unique} distinct rows), {len(cfg.widths)} widths, {n_inj} injections",
             "ms_per_search": t * 1e3, "trials_per_s": cfg.n_trials / t, "candidates": int(len(cand)),
             "injections_recovered": int(hit.sum()), "injection_recall": float(hit.mean()),
             "recall_interval_95": wilson(int(hit.sum()), len(inj)),
@@ -728,7 +739,7 @@ def stress_section(native, synth, steps: int, seed: int = 0):
             "false_alarm_pixels": fa, "false_alarm_fraction": fa / float(cfg.n_pix - len(inj)),
             "false_alarm_pixels_above_7.2": fa72,
             "roofline": {"bound": "alu", "achieved": ops / tk / 1e12, "peak": peak_ops / 1e12, "unit": "TFLOP/s",
-                         "frac": ops / tk / peak_ops, "kernel": f"{search_kernel_name(cfg.n_t, 'bf16', 'mad')} (MAD normalisation)",
+                         "frac": ops / tk / peak_ops, "kernel": search_kernel_name(cfg.n_t, 'bf16', 'mad', tile),
                          "kernel_ms": tk * 1e3, "ops_per_launch": ops, "tile": tile, "tile_ms": tile_ms},
             "hbm": {"achieved_gbs": alg_bytes / tk / 1e9, "frac": alg_bytes / tk / 1e9 / pk["hbm_gbs"],
                     "bytes_per_launch": alg_bytes},
@@ -738,7 +749,9 @@ def stress_section(native, synth, steps: int, seed: int = 0):
 # ----------------------------------------------------------------------------- GPU arm
 
 def main():
+    global SERVING_FIELDS
     args = parse()
+    SERVING_FIELDS = tuple(tuple(int(v) for v in f.split("x")) for f in args.serving_fields.split(","))
     if args.impl == "reference":
         return reference_arm(args)
     import torch
@@ -852,7 +865,7 @@ def main():
         imager = imager_section(native, args.imager_steps, seed=args.seed)
     stress = None
     if args.stress_steps > 0 and rank == 0:
-        stress = stress_section(native, synth, args.stress_steps, seed=args.seed)
+        stress = stress_section(native, synth, args.stress_steps, seed=args.seed, size=args.stress_size)
 
     pk = peaks()
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -875,7 +888,7 @@ def main():
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                      "unit": "TFLOP/s", "frac": achieved / peak_ops,
                      "traffic": measured_traffic(cfg.ny, cfg.nx, args.dtype),
-                     "kernel": search_kernel_name(cfg.n_t, args.dtype),
+                     "kernel": search_kernel_name(cfg.n_t, args.dtype, tile=tile),
                      "kernel_ms": kern_s * 1e3, "tile": tile, "tile_ms": tile_ms,
                      "ops_per_launch": ops, "peak_basis": f"{n_sm} SM x 128 FP32 lanes x "
                      f"{pk['sm_max_mhz']:.0f} MHz ({pk['source']} max clock)"},

@@ -66,7 +66,11 @@ enum { NSFRB_OUT_CANDIDATES = 0, NSFRB_OUT_FULL = 1 };
 typedef struct {
     int32_t ny, nx;          /* image rows, columns (>= 1)                     */
     int32_t n_sub;           /* subbands, 1..32                                */
-    int32_t n_t;             /* window length in samples, 1..1247              */
+    int32_t n_t;             /* window length in samples, 1..1247: a warp holds
+                                a DM row's prefix sums over the whole window
+                                (32 lanes x at most 39 samples); the paper's
+                                windows are 25 and 1200 samples; longer ones
+                                are refused (EINVAL)                            */
     double t_samp_ms;        /* sampling time, e.g. 134.2                      */
     double k_dm_ms;          /* dispersion constant in ms GHz^2, e.g. 4.149    */
     const double *freq_mhz;  /* [n_sub] subband centres, strictly increasing   */
