@@ -256,21 +256,19 @@ __device__ __forceinline__ int generic_find(const float *Pw, int w, int L, int t
     return INT_MAX;
 }
 
-// Serving (at most 32 new trial ends per width): lane j takes the trial t = t_lo + j, with no loop
-// and no branch; lanes past the last trial give -inf.
-__device__ __forceinline__ float masked_max32(const float *Pw, int w, int L, int t_lo, int lane) {
-    const int t = t_lo + lane;
-    const bool ok = t + w <= L;
-    const int ti = ok ? t : 0;
-    const float b = Pw[ti + (ok ? w : 0)] - Pw[ti];
-    return ok ? b : neg_inf();
+// Serving (at most 32 new trial ends per width, nb = new_blk <= 32): lane j takes, for every width
+// w, the trial whose boxcar ends at the same prefix index e = L - nb + 1 + j (t = e - w), so P[e] is
+// read once per row; lanes j >= nb, and trials with t < 0, give -inf.  The trials are those of
+// t in [max(0, L - w - nb + 1), L - w], and each S/N is P[t + w] - P[t] as in every other path.
+__device__ __forceinline__ int masked_end(int L, int nb, int lane) {
+    const int e = L - nb + 1 + lane;
+    return (lane < nb && e >= 0) ? e : -1;
 }
 
-__device__ __forceinline__ int masked_find32(const float *Pw, int w, int L, int t_lo, int lane, float inv, float target) {
-    const int t = t_lo + lane;
-    const bool ok = t + w <= L;
-    const int ti = ok ? t : 0;
-    const float b = Pw[ti + (ok ? w : 0)] - Pw[ti];
+__device__ __forceinline__ int masked_find32(const float *Pw, int w, int e, float inv, float target) {
+    const int t = e - w;
+    const bool ok = e >= 0 && t >= 0;
+    const float b = Pw[ok ? e : 0] - Pw[ok ? t : 0];
     return (ok && b * inv == target) ? t : INT_MAX;
 }
 
@@ -588,23 +586,31 @@ __device__ __forceinline__ float large_max_pk(const float2 (&Ps)[C / 2]) {
 
 // ------------------------------------------------------------------ one warp, one pixel
 
+// Called by a warp (all lanes) once it has read the pixel's rows for the last time: after the
+// de-dispersion of its last row, or at once when its group is empty.  The barrier-free kernel
+// uses it to start the next copy into the buffer early; the other callers pass this no-op.
+struct NoReadDone {
+    __device__ __forceinline__ void operator()() const {}
+};
+
 // The search of one warp over the distinct DM rows [u_lo, u_hi) of one pixel whose
 // subband rows are in xs (pitch Tp, -inf beyond the window): de-dispersion by row
 // differences, prefix sums, the boxcars of every width class, the warp arg-max and,
 // when a row improves the warp's best, the earliest sample reaching it (re-evaluated
 // with the same operations).  FULL also writes every (DM, width) result of the rows.
 // Returns the warp's best (snr, distinct row u, width index, t) on every lane.
-template <int C, bool FULL>
+template <int C, bool FULL, typename OnRead = NoReadDone>
 __device__ __forceinline__ PixRec search_rows(const SearchParams &p, const float *xs, float *Pw, const float *s_inv,
                                               const int32_t *s_info, const int32_t *s_delta,
                                               const int32_t *s_shift, int u_lo, int u_hi, int64_t pix,
-                                              int lane) {
+                                              int lane, OnRead on_read = OnRead{}) {
     constexpr int SH = (C < kSmallMax) ? C : kSmallMax;
     const int n_sub = p.n_sub, n_t = p.n_t, Tp = p.Tp;
     const int t0 = lane * C;
     float bsnr = neg_inf();
     int bu = -1, bwi = -1, bt = -1;
     float D[C];
+    if (u_lo >= u_hi) on_read();
 #pragma unroll 1
     for (int u = u_lo; u < u_hi; ++u) {
         const int32_t *info = s_info + u * kInfo;
@@ -630,6 +636,7 @@ __device__ __forceinline__ PixRec search_rows(const SearchParams &p, const float
                 for (int c = 0; c < C; ++c) D[c] = (D[c] + xn[c]) - xo[c];
             }
         }
+        if (u == u_hi - 1) on_read();
         const int L = n_t - info[UI_SMAX];
 
         // in-lane prefix, warp scan of lane totals, P to shared memory
@@ -803,7 +810,7 @@ __device__ __forceinline__ int find_t_even(const SearchParams &p, const float2 (
     const int w = p.widths[wi];
     int t;
     if (masked && p.new_blk <= 32) {
-        t = masked_find32(Pw, w, L, max(0, L - w - p.new_blk + 1), lane, inv, target);
+        t = masked_find32(Pw, w, masked_end(L, p.new_blk, lane), inv, target);
     } else if (masked || p.wclass[wi] == WC_GENERIC) {
         const int tl = masked ? max(0, L - w - p.new_blk + 1) : 0;
         t = generic_find(Pw, w, L, tl, lane, inv, target);
@@ -825,12 +832,12 @@ __device__ __forceinline__ int find_t_even(const SearchParams &p, const float2 (
 // search_rows for even chunks (sample pairs, see above).  The pixel's rows are in storage ST
 // (0 FP32, 1 BF16, 2 FP16) with the window at element eoff of each row; with mask_tail the
 // elements past the window are not -inf and the de-dispersed samples past L are set to -inf.
-template <int C, bool FULL, int ST = 0>
+template <int C, bool FULL, int ST = 0, typename OnRead = NoReadDone>
 __device__ __forceinline__ PixRec search_rows_even(const SearchParams &p, const void *xs, float *Pw,
                                                    const float *s_inv, const int32_t *s_info,
                                                    const int32_t *s_delta, const int32_t *s_shift, int u_lo,
                                                    int u_hi, int64_t pix, int lane, int eoff = 0,
-                                                   bool mask_tail = false) {
+                                                   bool mask_tail = false, OnRead on_read = OnRead{}) {
     static_assert(C % 2 == 0, "even chunks only");
     constexpr int SH = (C < kSmallMax) ? C : kSmallMax;
     const int n_sub = p.n_sub, n_t = p.n_t, Tp = p.Tp;
@@ -840,6 +847,7 @@ __device__ __forceinline__ PixRec search_rows_even(const SearchParams &p, const 
     float bsnr = neg_inf();
     int bu = -1, bwi = -1, bt = -1;
     float2 D[C / 2];
+    if (u_lo >= u_hi) on_read();
 #pragma unroll 1
     for (int u = u_lo; u < u_hi; ++u) {
         const int32_t *info = s_info + u * kInfo;
@@ -847,8 +855,10 @@ __device__ __forceinline__ PixRec search_rows_even(const SearchParams &p, const 
             dd_first<C, ST>(D, xs, Tp, n_sub, s_shift + u * n_sub, te);
         else
             dd_delta<C, ST>(D, xs, Tp, s_delta, info[UI_DOFF], info[UI_ND], te);
+        if (u == u_hi - 1) on_read();
         const int L = n_t - info[UI_SMAX];
-        if (mask_tail) {
+        // (a masked search reads P only up to P[L], which needs no sample past L)
+        if (mask_tail && !masked) {
 #pragma unroll
             for (int m = 0; m < C / 2; ++m) {
                 if (t0 + 2 * m >= L) D[m].x = neg_inf();
@@ -925,12 +935,17 @@ __device__ __forceinline__ PixRec search_rows_even(const SearchParams &p, const 
 #undef NSFRB_LARGE_PK
         }
         if (masked && p.new_blk <= 32) {
-            // serving: every width's trials that end in the newest block, one per lane; ascending
-            // width order with a strict '>' keeps the smallest width index on ties
+            // serving: every width's trials that end in the newest block, one per lane, all ending at
+            // this lane's P index e; ascending width order with a strict '>' keeps the smallest width
+            // index on ties
+            const int e = masked_end(L, p.new_blk, lane);
+            const float pe = Pw[e >= 0 ? e : 0];
 #pragma unroll 4
             for (int wi = 0; wi < p.n_w; ++wi) {
-                const int w = p.widths[wi];
-                const float s = masked_max32(Pw, w, L, max(0, L - w - p.new_blk + 1), lane) * s_inv[wi];
+                const int t = e - p.widths[wi];
+                const bool ok = e >= 0 && t >= 0;
+                const float b = pe - Pw[ok ? t : 0];
+                const float s = ok ? b * s_inv[wi] : neg_inf();
                 if (s > ls) {
                     ls = s;
                     lw = wi;
@@ -984,18 +999,19 @@ __device__ __forceinline__ PixRec search_rows_even(const SearchParams &p, const 
 }
 
 // Per-warp row search for chunk size C (pairs for even C).  Odd chunks read FP32 rows only.
-template <int C, bool FULL, int ST = 0>
+template <int C, bool FULL, int ST = 0, typename OnRead = NoReadDone>
 __device__ __forceinline__ PixRec search_rows_any(const SearchParams &p, const void *xs, float *Pw, const float *s_inv,
                                                   const int32_t *s_info, const int32_t *s_delta,
                                                   const int32_t *s_shift, int u_lo, int u_hi, int64_t pix,
-                                                  int lane, int eoff = 0, bool mask_tail = false) {
+                                                  int lane, int eoff = 0, bool mask_tail = false,
+                                                  OnRead on_read = OnRead{}) {
     if constexpr (C % 2 == 0) {
-        return search_rows_even<C, FULL, ST>(p, xs, Pw, s_inv, s_info, s_delta, s_shift, u_lo, u_hi, pix, lane,
-                                             eoff, mask_tail);
+        return search_rows_even<C, FULL, ST, OnRead>(p, xs, Pw, s_inv, s_info, s_delta, s_shift, u_lo, u_hi, pix,
+                                                     lane, eoff, mask_tail, on_read);
     } else {
         static_assert(ST == 0, "odd chunks read FP32 rows");
-        return search_rows<C, FULL>(p, static_cast<const float *>(xs) + eoff, Pw, s_inv, s_info, s_delta, s_shift,
-                                    u_lo, u_hi, pix, lane);
+        return search_rows<C, FULL, OnRead>(p, static_cast<const float *>(xs) + eoff, Pw, s_inv, s_info, s_delta,
+                                            s_shift, u_lo, u_hi, pix, lane, on_read);
     }
 }
 
@@ -1246,9 +1262,13 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel(const __grid_consta
 // counts itself done; the last warp of a pixel combines the groups in row order (the DM tie rule),
 // writes the pixel's record, and starts the copy of the team's pixel two ahead into the buffer it
 // frees (with that pixel's 1 / (sigma sqrt(w))).  Warps of a team drift apart by at most one pixel.
-// With NB = 1 buffer per team the copy of the team's next pixel starts only when a pixel is done
-// (the team waits for it, the other team keeps the SM busy): for tiles too large for two buffers
-// per team.
+// With NB = 1 buffer per team (tiles too large for two buffers per team) the copy of the team's
+// next pixel starts when the pixel is done, or, for FP32 rows (copies of twice the bytes), as soon
+// as every warp of the team has read the pixel's rows for the last time (after the de-dispersion
+// of its last row), while the team still runs the boxcars of those rows.  (Measured on the
+// full-window workload: 6.82 -> 6.62 ms for FP32 rows, but 5.58 -> 6.06 ms for BF16 rows, which
+// keep the copy at the end of the pixel.)  A pixel's records and 1 / (sigma sqrt(w)) live in one
+// of two record slots per team, alternating by pixel; its rows in the buffer.
 // ST is the storage type of the rows, kept as they are in shared memory: FP32, or BF16 / FP16 read
 // in place by the mixed-precision adds (no widening pass).  A window that starts at any sample t_off
 // is copied from the 16-byte boundary below it and read from element eoff = t_off mod (16 / size)
@@ -1260,6 +1280,7 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel_pipe(const __grid_c
     constexpr int kEs = (ST == 0) ? 4 : 2;          // bytes per stored sample
     constexpr int kEpv = 16 / kEs;                  // samples per 16 bytes
     constexpr int W = kWarps / TEAMS;               // warps (and row groups) per team
+    constexpr bool kEarly = NB == 1 && ST == 0;     // next copy started once the rows are read
     static_assert(kWarps % TEAMS == 0, "teams divide the warps");
     const SmemLayout lay = smem_layout(p, C);
     int32_t *s_table = reinterpret_cast<int32_t *>(smem + lay.table);
@@ -1269,6 +1290,7 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel_pipe(const __grid_c
     float *s_inv = reinterpret_cast<float *>(smem + lay.sinv);             // [TEAMS][2][kMaxW]
     int32_t *s_cnt = reinterpret_cast<int32_t *>(smem + lay.sinv + sizeof(float) * kMaxW * 2 * TEAMS);
     int32_t *s_flag = s_cnt + 2 * TEAMS;    // error seen by a warp
+    int32_t *s_rd = s_flag + 1;             // [TEAMS] warps done reading the team's buffer (NB = 1)
     unsigned long long *s_bar = reinterpret_cast<unsigned long long *>(smem + lay.bar);   // [TEAMS][2]
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1301,15 +1323,16 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel_pipe(const __grid_c
     auto item_pixel = [&](int64_t it) -> int64_t {
         return p.pix_list ? static_cast<int64_t>(p.pix_list[it]) : p.pix0 + it;
     };
-    // slot (team, b): buffer, barrier, records, 1 / (sigma sqrt(w)) and done counter of one pixel
+    // buffer slot (team, b): pixel buffer and barrier; record slot (team, i mod 2): records,
+    // 1 / (sigma sqrt(w)) and done counter of the team's i-th pixel (with NB = 2 the two coincide)
     const int slot0 = NB * team;
-    // one warp: 1 / (sigma sqrt(w)) of item `it` into slot s, then its rows into buffer s
+    // one warp: 1 / (sigma sqrt(w)) of item `it` into record slot rs, then its rows into buffer sl
     // (lane 0 arms the barrier, lane k copies subband k)
-    auto issue_warp = [&](int64_t it, int sl) {
+    auto issue_warp = [&](int64_t it, int sl, int rs) {
         const int64_t pix = item_pixel(it);
         if (lane < p.n_w) {
             const float sg = p.sigma ? p.sigma[pix] : p.sigma_default;
-            s_inv[sl * kMaxW + lane] = 1.0f / (sg * sqrtf(static_cast<float>(p.widths[lane])));
+            s_inv[rs * kMaxW + lane] = 1.0f / (sg * sqrtf(static_cast<float>(p.widths[lane])));
         }
         __syncwarp();
         const uint32_t bytes = static_cast<uint32_t>(row_elems * kEs);
@@ -1323,10 +1346,9 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel_pipe(const __grid_c
                      &s_bar[sl]);
     };
     if (tid == 0) {
-        for (int sl = 0; sl < NB * TEAMS; ++sl) {
-            mbar_init(&s_bar[sl], 1);
-            s_cnt[sl] = 0;
-        }
+        for (int sl = 0; sl < NB * TEAMS; ++sl) mbar_init(&s_bar[sl], 1);
+        for (int rs = 0; rs < 2 * TEAMS; ++rs) s_cnt[rs] = 0;
+        for (int t = 0; t < TEAMS; ++t) s_rd[t] = 0;
         s_flag[0] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_proxy_async();
@@ -1336,8 +1358,8 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel_pipe(const __grid_c
     const int64_t G = static_cast<int64_t>(gridDim.x) * TEAMS;
     const int64_t it0 = static_cast<int64_t>(blockIdx.x) * TEAMS + team;
     if (wt == 0) {
-        if (it0 < n_items) issue_warp(it0, slot0);
-        if (NB == 2 && it0 + G < n_items) issue_warp(it0 + G, slot0 + 1);
+        if (it0 < n_items) issue_warp(it0, slot0, 2 * team);
+        if (NB == 2 && it0 + G < n_items) issue_warp(it0 + G, slot0 + 1, 2 * team + 1);
     }
 
     const int n_ua = p.n_u_active;
@@ -1345,7 +1367,7 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel_pipe(const __grid_c
     int issued_last = -1;   // local index of the last item whose copy this warp started
     int i = 0;
     for (int64_t it = it0; it < n_items; it += G, ++i) {
-        const int b = i % NB, sl = slot0 + b;
+        const int b = i % NB, sl = slot0 + b, rs = 2 * team + (i & 1);
         if (*reinterpret_cast<volatile int32_t *>(s_flag)) break;
         if (!mbar_wait(&s_bar[sl], static_cast<uint32_t>(i / NB) & 1u)) {
             if (lane == 0) {
@@ -1357,15 +1379,44 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel_pipe(const __grid_c
         const int g = (wt + i) % W;
         const int u_lo = (g * n_ua) / W, u_hi = ((g + 1) * n_ua) / W;
         const int64_t pix = item_pixel(it);
-        const PixRec wr = search_rows_any<C, false, ST>(p, s_xs + sl * buf_bytes, Pw, s_inv + sl * kMaxW, s_info,
-                                                        s_delta, s_shift, u_lo, u_hi, pix, lane, eoff, mask_tail);
+        // kEarly: the last warp of the team to read buffer sl for this pixel starts the copy of the
+        // team's next pixel into it (its 1 / (sigma sqrt(w)) into the other record slot); each warp's
+        // reads of the buffer are done before the async-proxy copy that refills it
+        auto read_done = [&]() {
+            if constexpr (kEarly) {
+                fence_proxy_async();
+                int lastr = 0;
+                if (lane == 0) {
+                    __threadfence_block();
+                    lastr = atomicAdd(&s_rd[team], 1) == W - 1;
+                    __threadfence_block();
+                }
+                lastr = __shfl_sync(kFull, lastr, 0);
+                if (lastr) {
+                    if (lane == 0) s_rd[team] = 0;
+                    __syncwarp();
+                    if (it + G < n_items) {
+                        issue_warp(it + G, sl, 2 * team + ((i + 1) & 1));
+                        issued_last = i + 1;
+                    }
+                }
+                __syncwarp();
+            }
+        };
+        PixRec wr;
+        if constexpr (kEarly)
+            wr = search_rows_any<C, false, ST>(p, s_xs + sl * buf_bytes, Pw, s_inv + rs * kMaxW, s_info, s_delta,
+                                               s_shift, u_lo, u_hi, pix, lane, eoff, mask_tail, read_done);
+        else
+            wr = search_rows_any<C, false, ST>(p, s_xs + sl * buf_bytes, Pw, s_inv + rs * kMaxW, s_info, s_delta,
+                                               s_shift, u_lo, u_hi, pix, lane, eoff, mask_tail);
         // publish; this warp's reads of buffer sl are done before the copy that refills it
         fence_proxy_async();
         int last = 0;
         if (lane == 0) {
-            s_wbest[sl * kWarps + g] = wr;
+            s_wbest[rs * kWarps + g] = wr;
             __threadfence_block();
-            last = atomicAdd(&s_cnt[sl], 1) == W - 1;
+            last = atomicAdd(&s_cnt[rs], 1) == W - 1;
             __threadfence_block();
         }
         last = __shfl_sync(kFull, last, 0);
@@ -1373,7 +1424,7 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel_pipe(const __grid_c
             if (lane == 0) {
                 PixRec best{neg_inf(), -1, -1, -1};
                 for (int q = 0; q < W; ++q) {
-                    const PixRec r = s_wbest[sl * kWarps + q];
+                    const PixRec r = s_wbest[rs * kWarps + q];
                     if (r.snr > best.snr) best = r;
                 }
                 if (best.dm_idx >= 0) best.dm_idx = s_info[best.dm_idx * kInfo + UI_FIRST_D];
@@ -1382,12 +1433,12 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel_pipe(const __grid_c
                     atomicOr(p.err, ERR_ZERO_MAD);
                 }
                 p.rec[pix] = best;
-                s_cnt[sl] = 0;
+                s_cnt[rs] = 0;
             }
             __syncwarp();
             const int64_t nxt = it + NB * G;
-            if (nxt < n_items) {
-                issue_warp(nxt, sl);
+            if (!kEarly && nxt < n_items) {
+                issue_warp(nxt, sl, 2 * team + ((i + NB) & 1));
                 issued_last = i + NB;
             }
         }
