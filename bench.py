@@ -32,6 +32,12 @@ METRIC = "pixel·DM·width S/N trials/s; % of GB300 HBM peak; p99 block latency 
 WORKLOAD = "full-window search 301x301 px x 16 sub x 1200 samples, 64 DM 0-2000, 12 widths 1..1024+1200"
 
 
+def workload_name(cfg) -> str:
+    """The workload's name with its sizes (the default is WORKLOAD)."""
+    return (f"full-window search {cfg.ny}x{cfg.nx} px x {cfg.n_sub} sub x {cfg.n_t} samples, "
+            f"{len(cfg.dm)} DM 0-2000, {len(cfg.widths)} widths 1..1024+1200")
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -41,6 +47,8 @@ def parse():
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16"])
     ap.add_argument("--ny", type=int, default=301)
     ap.add_argument("--nx", type=int, default=301)
+    ap.add_argument("--n-t", type=int, default=1200,
+                    help="window length in samples (1200 is the workload; up to 4096)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving-blocks", type=int, default=40,
@@ -145,8 +153,10 @@ def search_kernel_name(n_t, dtype, noise="known", tile=None):
     rows read in place when C is even and the rows fill whole 16-byte units), with the pixel x DM
     tile (teams, buffers per team) the plan chose; MAD normalisation is a pass of its own into FP32
     slabs that the barrier-free kernel then searches."""
-    c = next(c for c in (1, 3, 5, 9, 17, 25, 38, 39) if 32 * c >= n_t + 1)
     st = {"f32": 0, "bf16": 1, "f16": 2}[dtype]
+    if n_t > 1247:   # beyond the register path: the long-window kernel (MAD slabs are FP32)
+        return f"search_kernel_long<{0 if noise == 'mad' else st}, false>"
+    c = next(c for c in (1, 3, 5, 9, 17, 25, 38, 39) if 32 * c >= n_t + 1)
     tt = "" if tile is None else f", {int(tile) // 10}, {int(tile) % 10}"
     if noise == "mad":
         return f"mad_normalise_kernel + search_kernel_pipe<{c}, 0{tt}> (FP32 slabs)"
@@ -272,7 +282,7 @@ def reference_arm(args):
     if rank != 0:
         return 0
     from paper_2510_18136_gb300 import synth
-    cfg = synth.config_full_window(args.ny, args.nx)
+    cfg = synth.config_full_window(args.ny, args.nx, n_t=args.n_t)
     cfg.sigma_pix = synth.psf_sigma()
     import oracle
     host = synth.psf_noise(cfg, args.seed)          # CPU generation, same recipe
@@ -300,7 +310,7 @@ def reference_arm(args):
     line = {"metric": METRIC, "value": value, "unit": "trials/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "kind": "FP64 CPU oracle", "injections": len(inj),
+            "config": {"workload": workload_name(cfg), "kind": "FP64 CPU oracle", "injections": len(inj),
                        "step": f"{int(np.median(ns))} random pixels of the cube searched per step"},
             "sample_pixels_per_step": int(np.median(ns)), "sample_trials_per_step": int(np.median(ns)) * 64 * 12,
             "cpu_baseline": {"value": value, "unit": "trials/s", "cores": cores, "kind": "oracle",
@@ -770,7 +780,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
 
-    cfg = synth.config_full_window(args.ny, args.nx)
+    cfg = synth.config_full_window(args.ny, args.nx, n_t=args.n_t)
     cfg.sigma_pix = synth.psf_sigma()
     cube, inj = make_cube(native, synth, cfg, args.seed + rank, dev, args.dtype)
     sigma = torch.full((cfg.n_pix,), cfg.sigma_pix * math.sqrt(cfg.n_sub), device=dev)
@@ -878,7 +888,7 @@ def main():
         "metric": METRIC, "value": value, "unit": "trials/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": elapsed_max / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
-        "config": {"workload": WORKLOAD, "ny": cfg.ny, "nx": cfg.nx, "n_sub": cfg.n_sub, "n_t": cfg.n_t,
+        "config": {"workload": workload_name(cfg), "ny": cfg.ny, "nx": cfg.nx, "n_sub": cfg.n_sub, "n_t": cfg.n_t,
                    "n_dm": len(cfg.dm), "n_unique_dm_rows": n_unique, "widths": [int(w) for w in cfg.widths],
                    "storage": args.dtype, "noise": "known sigma", "l2": "inputs larger than L2 (cube "
                    f"{alg_bytes / 1e9:.2f} GB)",

@@ -66,11 +66,11 @@ enum { NSFRB_OUT_CANDIDATES = 0, NSFRB_OUT_FULL = 1 };
 typedef struct {
     int32_t ny, nx;          /* image rows, columns (>= 1)                     */
     int32_t n_sub;           /* subbands, 1..32                                */
-    int32_t n_t;             /* window length in samples, 1..1247: a warp holds
-                                a DM row's prefix sums over the whole window
-                                (32 lanes x at most 39 samples); the paper's
-                                windows are 25 and 1200 samples; longer ones
-                                are refused (EINVAL)                            */
+    int32_t n_t;             /* window length in samples, 1..4096.  Up to 1247
+                                (the paper's 25 and 1200) a warp holds a DM
+                                row's prefix sums in registers; longer windows
+                                run a kernel that reads the cube in place and
+                                keeps the prefix sums in shared memory          */
     double t_samp_ms;        /* sampling time, e.g. 134.2                      */
     double k_dm_ms;          /* dispersion constant in ms GHz^2, e.g. 4.149    */
     const double *freq_mhz;  /* [n_sub] subband centres, strictly increasing   */
@@ -190,7 +190,7 @@ nsfrb_status nsfrb_plan_get_tile(nsfrb_plan_t plan, int32_t dtype, int32_t *tile
  * one with the smallest median search time as the plan's preference for the
  * storage type the kernel searched.  h_tile (or NULL) gets that tile (0 when
  * the plan's searches do not use this kernel: FULL output, MAD windows of
- * n_t not a multiple of 4); h_ms[NSFRB_N_TILES] (or NULL) the medians in
+ * n_t not a multiple of 4, windows over 1247 samples); h_ms[NSFRB_N_TILES] (or NULL) the medians in
  * NSFRB_TILES order, -1 for tiles that do not fit.  Synchronous: it waits
  * for every search it queues on `stream`.  Afterwards the plan's results are
  * those of one search of the cube with the chosen tile.  Errors: as
@@ -266,7 +266,9 @@ nsfrb_status nsfrb_psf_cluster(const nsfrb_candidate *d_cand, int32_t n, int32_t
  *                  MAD row was met (MAD mode), -2 if a bulk copy timed out.
  * Asynchronous on `stream`.  Limits: ny*nx <= NSFRB_STATIC_MAX_PIX and the
  * plan's tables <= NSFRB_STATIC_MAX_TABLE_WORDS int32 words (EINVAL beyond);
- * candidate output mode only; no re-scoring.  The first call on a device
+ * candidate output mode only; no re-scoring; MAD normalisation only for
+ * windows of at most 1247 samples (longer ones need nsfrb_search's
+ * normalisation workspace: EINVAL).  The first call on a device
  * looks up the array's device address there (and sets the kernel's shared
  * memory limit), so make that first call before any stream capture.  The
  * array is reserved on a device when the library's code for this call is

@@ -319,14 +319,13 @@ struct RowView {
     }
 };
 
-// Shared memory of one warp: its row buffer (kMaxT + 1 samples, as stored), histogram, gather space.
-template <int ST>
-__host__ __device__ constexpr size_t row_buf_bytes() {
-    return (((ST == 0 ? 4 : 2) * static_cast<size_t>(kMaxT + 1) + 15) / 16) * 16;
+// Shared memory of one warp: its row buffer (n_t + 1 samples of es bytes, as stored), histogram,
+// gather space.
+__host__ __device__ inline size_t row_buf_bytes(int es, int n_t) {
+    return ((static_cast<size_t>(es) * static_cast<size_t>(n_t + 1) + 15) / 16) * 16;
 }
-template <int ST>
-__host__ __device__ constexpr size_t warp_smem_bytes() {
-    return row_buf_bytes<ST>() + sizeof(uint32_t) * (kBins + 4) + sizeof(float) * (32 * kColPitch + 32);
+__host__ __device__ inline size_t warp_smem_bytes(int es, int n_t) {
+    return row_buf_bytes(es, n_t) + sizeof(uint32_t) * (kBins + 4) + sizeof(float) * (32 * kColPitch + 32);
 }
 
 // VEC: rows copied by 16-byte loads (16-byte aligned cube and output, rows of whole 16 bytes).
@@ -338,10 +337,10 @@ __global__ void __launch_bounds__(kMadWarps * 32) mad_normalise_kernel(const voi
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int kEs = ST == 0 ? 4 : 2;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned char *mine = smem + warp * warp_smem_bytes<ST>();
+    unsigned char *mine = smem + warp * warp_smem_bytes(kEs, n_t);
     void *row = mine;
     Scratch sc;
-    sc.hist = reinterpret_cast<uint32_t *>(mine + row_buf_bytes<ST>());
+    sc.hist = reinterpret_cast<uint32_t *>(mine + row_buf_bytes(kEs, n_t));
     sc.cols = reinterpret_cast<float *>(sc.hist + kBins + 4);
     sc.list = sc.cols + 32 * kColPitch;
     const float kInf = __int_as_float(0x7f800000);
@@ -459,7 +458,7 @@ __global__ void __launch_bounds__(kMadWarps * 32) mad_normalise_kernel(const voi
 template <int ST, bool VEC>
 cudaError_t launch_mad(const void *cube, int64_t pix0, int64_t n_pix, int n_sub, int n_t, float *out, uint8_t *bad,
                        int n_sm, cudaStream_t s) {
-    const size_t smem = kMadWarps * warp_smem_bytes<ST>();
+    const size_t smem = kMadWarps * warp_smem_bytes(ST == 0 ? 4 : 2, n_t);
     cudaError_t e = cudaFuncSetAttribute(mad_normalise_kernel<ST, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;

@@ -13,7 +13,9 @@ constexpr int kWarps = 12;                // warps per search CTA
 constexpr int kThreads = kWarps * 32;     // threads per search CTA
 constexpr int kMaxW = 16;                 // widths per plan
 constexpr int kMaxSub = 32;               // subbands per plan
-constexpr int kMaxT = 1247;               // longest window (32 lanes x 39 samples - 1)
+constexpr int kMaxT = 4096;               // longest window
+constexpr int kMaxTRegs = 1247;           // longest window of the register path (32 lanes x 39 samples - 1)
+constexpr int kLongC = 128;               // "chunk" of longer windows: the long-window kernel
 constexpr int kSmallMax = 16;             // widths <= min(C, 16) use the in-lane path
 constexpr int kHistBins = 256;            // radix-select digit bins (MAD mode)
 
@@ -90,8 +92,8 @@ struct SearchParams {
     int32_t n_dm;
     int32_t new_blk;       // > 0: only trials that end in the last new_blk samples
     int32_t pipe;          // 1: barrier-free kernel (stage 1 or 3, KNOWN noise, records only)
-    int32_t teams;         // barrier-free kernel: 1 (all warps on one pixel at a time) or 2 (two
-                           // teams of half the warps, each on its own pixel with its own buffers)
+    int32_t teams;         // barrier-free kernel: teams of kWarps / teams warps, each on its own
+                           // pixel with its own buffers; long-window kernel: warps per CTA
     int32_t nb;            // barrier-free kernel: pixel buffers per team, 2 (the pixel after next
                            // copied while one is searched) or 1 (the next copied after a pixel)
     // ---- outputs (indexed by absolute pixel)
@@ -150,12 +152,17 @@ constexpr int kNumChunks = 8;
 inline int pick_chunk(int n_t) {
     for (int i = 0; i < kNumChunks; ++i)
         if (32 * kChunks[i] >= n_t + 1) return kChunks[i];
-    return -1;
+    return n_t <= kMaxT ? kLongC : -1;
 }
 
-// Kernel launchers (one translation unit per chunk size).
+// Kernel launchers (one translation unit per chunk size; C = kLongC: the long-window kernel).
 cudaError_t launch_search(int C, const SearchParams &p, int grid, size_t smem, cudaStream_t s);
 cudaError_t prepare_search(int C, size_t smem);
+// The long-window kernel: warps per CTA that fit max_smem (0: none), and its shared memory.
+int long_warps(const SearchParams &p, int max_smem);
+size_t long_smem(const SearchParams &p, int n_warps);
+cudaError_t launch_search_long(const SearchParams &p, int grid, size_t smem, cudaStream_t s);
+cudaError_t prepare_search_long(size_t smem);
 
 // Compaction of per-pixel records into the candidate list ordered by pixel.
 cudaError_t launch_compact(const PixRec *rec, int64_t n_pix, int32_t nx, float thr,

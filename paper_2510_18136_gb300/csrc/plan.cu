@@ -45,6 +45,7 @@ cudaError_t launch_search(int C, const SearchParams &p, int grid, size_t smem, c
         case 25: return launch_search_c25(p, grid, smem, s);
         case 38: return launch_search_c38(p, grid, smem, s);
         case 39: return launch_search_c39(p, grid, smem, s);
+        case kLongC: return launch_search_long(p, grid, smem, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -59,6 +60,7 @@ cudaError_t prepare_search(int C, size_t smem) {
         case 25: return prepare_search_c25(smem);
         case 38: return prepare_search_c38(smem);
         case 39: return prepare_search_c39(smem);
+        case kLongC: return prepare_search_long(smem);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -115,6 +117,17 @@ bool tile_is_known(int t) {
 }
 
 bool choose_stage_for(int C, int max_smem, SearchParams &sp, size_t &smem, int tile_pref) {
+    if (C == kLongC) {
+        // windows beyond the register path: the long-window kernel reads the cube in place; its
+        // CTA takes as many warps as their prefix rows fit (the warp count travels in sp.teams)
+        sp.pipe = 0;
+        sp.stage = 0;
+        const int w = long_warps(sp, max_smem);
+        if (w < 1) return false;
+        sp.teams = w;
+        smem = long_smem(sp, w);
+        return true;
+    }
     const uintptr_t base = reinterpret_cast<uintptr_t>(sp.cube);
     const int n_t = sp.n_t;
     const int epv = 16 / static_cast<int>(elem_size(sp.dtype));   // samples per 16 bytes
@@ -283,7 +296,9 @@ nsfrb_status queue_search(nsfrb_plan_s *pl, const void *cube, int64_t cube_pix0,
 // rows do not fill whole 16-byte units.
 bool mad_slabs_apply(const nsfrb_plan_s *pl) {
     const nsfrb_config &c = pl->cfg;
-    return c.noise_mode == NSFRB_NOISE_MAD && c.out_mode == NSFRB_OUT_CANDIDATES && c.n_t % 4 == 0;
+    if (c.noise_mode != NSFRB_NOISE_MAD) return false;
+    // long windows: always (their kernel has no in-kernel selection), in either output mode
+    return pl->C == kLongC || (c.out_mode == NSFRB_OUT_CANDIDATES && c.n_t % 4 == 0);
 }
 
 nsfrb_status queue_search_mad(nsfrb_plan_s *pl, const void *cube, int dtype, int64_t pix0, int64_t n,
@@ -379,7 +394,7 @@ nsfrb_status nsfrb_plan(const nsfrb_config *cfg, nsfrb_plan_t *out) {
     if (c.ny < 1 || c.nx < 1) return fail(nullptr, NSFRB_EINVAL, "ny, nx must be >= 1");
     if (static_cast<int64_t>(c.ny) * c.nx > (int64_t(1) << 30)) return fail(nullptr, NSFRB_EINVAL, "too many pixels");
     if (c.n_sub < 1 || c.n_sub > kMaxSub) return fail(nullptr, NSFRB_EINVAL, "n_sub must be 1..32");
-    if (c.n_t < 1 || c.n_t > kMaxT) return fail(nullptr, NSFRB_EINVAL, "n_t must be 1..1247");
+    if (c.n_t < 1 || c.n_t > kMaxT) return fail(nullptr, NSFRB_EINVAL, "n_t must be 1..4096");
     if (!(c.t_samp_ms > 0.0) || !(c.k_dm_ms >= 0.0)) return fail(nullptr, NSFRB_EINVAL, "t_samp_ms, k_dm_ms");
     if (!c.freq_mhz || !c.dm || !c.widths) return fail(nullptr, NSFRB_EINVAL, "null table");
     if (c.n_dm < 1 || c.n_dm > 4096) return fail(nullptr, NSFRB_EINVAL, "n_dm must be 1..4096");
@@ -483,12 +498,14 @@ nsfrb_status nsfrb_plan(const nsfrb_config *cfg, nsfrb_plan_t *out) {
     for (int u = 0; u < pl->n_u_active; ++u) smax_active = std::max(smax_active, info[u * kInfo + UI_SMAX]);
     // a row holds the window from element eoff < 8 (a window start below a 16-byte boundary) up to
     // the last sample a lane chunk reads, 32 C + smax - 1, and one more
-    pl->Tp = static_cast<int>(align_up(static_cast<size_t>(32 * pl->C + smax_active + 1 + 7), 8));
+    const bool long_window = pl->C == kLongC;
+    pl->Tp = long_window ? 0 : static_cast<int>(align_up(static_cast<size_t>(32 * pl->C + smax_active + 1 + 7), 8));
     for (int i = 0; i < c.n_w; ++i) {
         const int w = pl->widths[i];
         pl->wclass[i] = WC_GENERIC;
-        for (int j = 0; j < kPow2; ++j)
-            if (w == (1 << j)) pl->wclass[i] = pow2_class(pl->C, j);
+        if (!long_window)
+            for (int j = 0; j < kPow2; ++j)
+                if (w == (1 << j)) pl->wclass[i] = pow2_class(pl->C, j);
     }
     // The plan must fit at least the plain staging scheme in 227 KB.
     {
@@ -501,7 +518,7 @@ nsfrb_status nsfrb_plan(const nsfrb_config *cfg, nsfrb_plan_t *out) {
         sp.n_deltas = pl->n_deltas;
         sp.noise_mode = c.noise_mode;
         sp.stage = 0;
-        if (smem_layout(sp, pl->C).total > 232448) {
+        if (long_window ? long_smem(sp, 1) > 232448 : smem_layout(sp, pl->C).total > 232448) {
             delete pl;
             return fail(nullptr, NSFRB_EINVAL, "plan tables and window do not fit in shared memory");
         }

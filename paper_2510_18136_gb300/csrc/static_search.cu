@@ -128,6 +128,8 @@ extern "C" nsfrb_status nsfrb_search_static(nsfrb_plan_t plan, const void *d_cub
         return fail(plan, NSFRB_EINVAL, "delay tables larger than NSFRB_STATIC_MAX_TABLE_WORDS");
     if (c.out_mode != NSFRB_OUT_CANDIDATES) return fail(plan, NSFRB_EINVAL, "candidate output mode only");
     if (c.noise_mode == NSFRB_NOISE_MAD && d_sigma) return fail(plan, NSFRB_EINVAL, "d_sigma must be NULL in MAD mode");
+    if (c.noise_mode == NSFRB_NOISE_MAD && plan->C == kLongC)
+        return fail(plan, NSFRB_EINVAL, "MAD normalisation of windows over 1247 samples needs nsfrb_search's workspace");
     if (plan->latched != NSFRB_OK) return fail(plan, plan->latched, "plan has a latched CUDA error");
 
     int dev = 0;

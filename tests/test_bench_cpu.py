@@ -38,5 +38,6 @@ def test_search_kernel_name_follows_the_chunk_rule():
         "mad_normalise_kernel + search_kernel_pipe<38, 0, 2, 1> (FP32 slabs)"
     assert bench.search_kernel_name(1200, "bf16", tile=41) == "search_kernel_pipe<38, 1, 4, 1>"
     assert bench.search_kernel_name(1247, "f32") == "search_kernel_pipe<39, 0>"
+    assert bench.search_kernel_name(4096, "bf16") == "search_kernel_long<1, false>"
     assert bench.search_kernel_name(64, "f32") == "search_kernel_pipe<3, 0>"
     assert bench.search_kernel_name(1001, "bf16") == "search_kernel<38, false>"

@@ -77,6 +77,21 @@ def test_invalid_configs_rejected(native, field, value):
     assert e.value.status == native.EINVAL
 
 
+@pytest.mark.parametrize("n_t", [1247, 1248, 4096])
+def test_window_lengths_up_to_4096_accepted(native, n_t):
+    """Windows of 1..4096 samples make plans (up to 1247 the register path, beyond it the
+    long-window kernel); 4097 is refused."""
+    cfg = synth.config_full_window(2, 2, n_t=n_t)
+    cfg.widths = np.array([1, 2, 1024, n_t], np.int32)
+    with native.Plan(cfg) as p:
+        assert p.delays().shape == (64, 16)
+    cfg.n_t = 4097
+    cfg.widths = np.array([1, 4097], np.int32)
+    with pytest.raises(native.NsfrbError) as e:
+        native.Plan(cfg)
+    assert e.value.status == native.EINVAL and "4096" in native.lib.nsfrb_last_error().decode()
+
+
 def test_unsorted_dm_and_widths_rejected(native):
     cfg = synth.config_small()
     cfg.dm = cfg.dm[::-1].copy()

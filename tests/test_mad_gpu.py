@@ -2,7 +2,7 @@
 sample equals the FP32 evaluation of the same formula from the exact order statistics (numpy sort),
 and lies within the FP32 rounding bound of the FP64 oracle.  Rows are chosen to stress the
 counting selection: ties, clusters far apart, signed zeros, huge dynamic range, sorted rows,
-spikes, zero MAD, and every row length class (scalar and 16-byte paths, one sample to 1247)."""
+spikes, zero MAD, and every row length class (scalar and 16-byte paths, one sample to 4096)."""
 import ctypes
 
 import numpy as np
@@ -78,7 +78,7 @@ def _expected_f32(xs):
 
 
 @pytest.mark.parametrize("dtype", ["f32", "bf16", "f16"])
-@pytest.mark.parametrize("n_t", [1, 2, 3, 31, 32, 33, 64, 100, 999, 1000, 1200, 1246, 1247])
+@pytest.mark.parametrize("n_t", [1, 2, 3, 31, 32, 33, 64, 100, 999, 1000, 1200, 1246, 1247, 2001, 4096])
 def test_mad_normalise_rows(native, dtype, n_t):
     tdt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[dtype]
     kinds = ["gauss", "student", "ties", "clusters", "zeros", "range", "sorted", "spikes", "constant"]
@@ -122,6 +122,6 @@ def test_mad_normalise_rejects_bad_sizes(native):
     d = torch.zeros(16, device="cuda")
     b = torch.zeros(4, dtype=torch.uint8, device="cuda")
     p = ctypes.c_void_p(d.data_ptr())
-    for n_rows, n_t, dt in ((0, 4, 0), (4, 0, 0), (1, 1248, 0), (4, 4, 3)):
+    for n_rows, n_t, dt in ((0, 4, 0), (4, 0, 0), (1, 4097, 0), (4, 4, 3)):
         assert native.lib.nsfrb_dbg_mad_normalise(p, dt, n_rows, n_t, p, ctypes.c_void_p(b.data_ptr()),
                                                   None) == native.EINVAL
