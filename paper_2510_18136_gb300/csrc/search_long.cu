@@ -21,8 +21,12 @@
 //  * Every width is then evaluated from P in shared memory (lane-strided trials), the warp's
 //    arg-max over widths taken, and the earliest sample reaching it found by re-evaluating the
 //    same operations.
-//  * Warps take rows w, w + n_warps, ... of the pixel; the CTA combines the warps' bests by
-//    (S/N, row) and writes the record (and, in FULL mode, every (DM, width) result).
+//  * Each warp takes a contiguous group of the pixel's distinct DM rows.  It builds the group's
+//    first row from every subband (all loads of a step issued before the sum) and each next row
+//    from the previous one by adding and subtracting only the subbands whose shift changed, with
+//    the previous row's D[t] = P[t + 1] - P[t] read back from its compensated prefix (exact to
+//    the rounding of D itself).  The CTA combines the warps' bests by (S/N, row) and writes the
+//    record (and, in FULL mode, every (DM, width) result).
 // Samples read past the window never enter a valid trial: a trial of row u ends before
 // L_u = n_t - smax_u, and D[t] for t >= L_u is not computed.
 #include <climits>
@@ -40,9 +44,9 @@ namespace dev {
 __host__ __device__ inline int long_ppitch(int n_t) { return static_cast<int>(align_up(static_cast<size_t>(n_t) + 33, 4)); }
 
 // Shared memory: tables | P rows, hi [n_warps][ppitch] FP32 and lo [n_warps][ppitch] FP16 | warp
-// bests | 1 / (sigma sqrt(w)) | per-warp subband row offsets.
+// bests | 1 / (sigma sqrt(w)).
 struct LongLayout {
-    size_t table, pbuf, plo, wbest, sinv, off, total;
+    size_t table, pbuf, plo, wbest, sinv, total;
 };
 
 __host__ __device__ inline LongLayout long_layout(const SearchParams &p, int n_warps) {
@@ -58,8 +62,6 @@ __host__ __device__ inline LongLayout long_layout(const SearchParams &p, int n_w
     o += sizeof(PixRec) * (size_t)n_warps;
     L.sinv = o;
     o += sizeof(float) * kMaxW;
-    L.off = o;
-    o += sizeof(int32_t) * (size_t)n_warps * p.n_sub;
     L.total = align_up(o, 16);
     return L;
 }
@@ -115,7 +117,6 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel_long(const __grid_c
     float *s_pbuf = reinterpret_cast<float *>(smem + lay.pbuf);
     PixRec *s_wbest = reinterpret_cast<PixRec *>(smem + lay.wbest);
     float *s_inv = reinterpret_cast<float *>(smem + lay.sinv);
-    int32_t *s_off = reinterpret_cast<int32_t *>(smem + lay.off);   // [n_warps][n_sub]
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n_sub = p.n_sub, n_t = p.n_t;
@@ -126,7 +127,6 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel_long(const __grid_c
     const int32_t *s_shift = s_table + p.n_u * kInfo + p.n_deltas;
     float *Pw = s_pbuf + (size_t)warp * long_ppitch(n_t);
     __half *Plo = reinterpret_cast<__half *>(smem + lay.plo) + (size_t)warp * long_ppitch(n_t);
-    int32_t *Ow = s_off + warp * n_sub;
     const size_t es = (ST == 0) ? 4 : 2;
     if (lane == 0) {
         Pw[0] = 0.0f;
@@ -153,29 +153,79 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel_long(const __grid_c
 
         float bsnr = neg_inf();
         int bu = -1, bwi = -1, bt = -1;
+        // the warp's rows: a contiguous group [u_lo, u_hi); its first row is built from every
+        // subband, each next row from the previous one by the subbands whose shift changed
+        const int u_lo = (warp * n_ua) / n_warps, u_hi = ((warp + 1) * n_ua) / n_warps;
+        const int32_t *s_delta = s_table + p.n_u * kInfo;
+        const int32_t rl = static_cast<int32_t>(p.row_len);
+        // sample tt of subband k of the pixel (tt < n_t)
+        auto xat = [&](int k, int tt) -> float {
+            if constexpr (ST >= 0)
+                return tile_x<ST>(tile, k * rl + t_off + tt);
+            else
+                return long_x_any(p, pix, k, tt, t_off);
+        };
 #pragma unroll 1
-        for (int u = bad ? n_ua : warp; u < n_ua; u += n_warps) {
+        for (int u = bad ? u_hi : u_lo; u < u_hi; ++u) {
             const int32_t *sh = s_shift + u * n_sub;
             const int32_t *info = s_info + u * kInfo;
             const int L = n_t - info[UI_SMAX];
-            if constexpr (ST >= 0) {
-                // per subband the offset of sample 0 of the shifted row within the tile
-                for (int k = lane; k < n_sub; k += 32) Ow[k] = k * static_cast<int32_t>(p.row_len) + t_off + sh[k];
-                __syncwarp();
-            }
-            // de-dispersion and compensated prefix, 32 samples per step
+            const bool first = u == u_lo;
+            const int d0 = info[UI_DOFF], nd = info[UI_ND];
+            // de-dispersion and compensated prefix, 32 samples per step.  A next row reads the
+            // previous row's D[t] = P[t + 1] - P[t] from the compensated prefix it overwrites:
+            // each lane reads the old pair at t + 1, takes the one at t from the lane below (lane 0
+            // from lane 31 of the step before), and writes the new pair at t + 1 afterwards.
             float run = 0.0f, run_lo = 0.0f;
+            float ph_prev = 0.0f, pl_prev = 0.0f;   // old pair at the step's first index
 #pragma unroll 1
             for (int t0 = 0; t0 < L; t0 += 32) {
                 const int t = t0 + lane;
                 float d = 0.0f;
-                if (t < L) {
-                    if constexpr (ST >= 0) {
-#pragma unroll 4
-                        for (int k = 0; k < n_sub; ++k) d += tile_x<ST>(tile, Ow[k] + t);
+                if (first) {
+                    if (t < L) {
+                        // every subband's load issued before the sum (in subband order)
+#pragma unroll
+                        for (int kk = 0; kk < kMaxSub; kk += 16) {
+                            if (kk >= n_sub) break;
+                            float xv[16];
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) xv[j] = (kk + j < n_sub) ? xat(kk + j, t + sh[kk + j]) : 0.0f;
+#pragma unroll
+                            for (int j = 0; j < 16; ++j)
+                                if (kk + j < n_sub) d += xv[j];
+                        }
+                    }
+                } else {
+                    const float oh = Pw[t + 1], ol = __half2float(Plo[t + 1]);
+                    float ph = __shfl_up_sync(kFull, oh, 1), pl = __shfl_up_sync(kFull, ol, 1);
+                    if (lane == 0) {
+                        ph = ph_prev;
+                        pl = pl_prev;
+                    }
+                    ph_prev = __shfl_sync(kFull, oh, 31);
+                    pl_prev = __shfl_sync(kFull, ol, 31);
+                    d = (oh - ph) + (ol - pl);
+                    if (t < L) {
+#pragma unroll 1
+                        for (int e0 = 0; e0 < nd; e0 += 2) {
+                            float xn[2], xo[2];
+#pragma unroll
+                            for (int j = 0; j < 2; ++j) {
+                                xn[j] = xo[j] = 0.0f;
+                                if (e0 + j < nd) {
+                                    const uint32_t pk = static_cast<uint32_t>(s_delta[d0 + e0 + j]);
+                                    const int k = pk & 63u, so = (pk >> 6) & 0x1fffu, sn = pk >> 19;
+                                    xn[j] = xat(k, t + sn);
+                                    xo[j] = xat(k, t + so);
+                                }
+                            }
+#pragma unroll
+                            for (int j = 0; j < 2; ++j)
+                                if (e0 + j < nd) d = (d + xn[j]) - xo[j];
+                        }
                     } else {
-#pragma unroll 4
-                        for (int k = 0; k < n_sub; ++k) d += long_x_any(p, pix, k, t + sh[k], t_off);
+                        d = 0.0f;
                     }
                 }
                 float v = d;
