@@ -178,23 +178,54 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel_long(const __grid_c
             // from lane 31 of the step before), and writes the new pair at t + 1 afterwards.
             float run = 0.0f, run_lo = 0.0f;
             float ph_prev = 0.0f, pl_prev = 0.0f;   // old pair at the step's first index
+            // the first two changed subbands of a next row (k, old and new shift), decoded once
+            int dk[2] = {0, 0}, dso[2] = {0, 0}, dsn[2] = {0, 0};
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+                if (!first && j < nd) {
+                    const uint32_t pk = static_cast<uint32_t>(s_delta[d0 + j]);
+                    dk[j] = pk & 63u;
+                    dso[j] = (pk >> 6) & 0x1fffu;
+                    dsn[j] = pk >> 19;
+                }
+            // the global loads of a step, issued one step ahead of its sum: a first row's first 16
+            // subbands, a next row's first two changed subbands (new and old sample)
+            float xa[16];
+            auto fetch = [&](int tt) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) xa[j] = 0.0f;
+                if (tt < L) {
+                    if (first) {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            if (j < n_sub) xa[j] = xat(j, tt + sh[j]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 2; ++j)
+                            if (j < nd) {
+                                xa[2 * j] = xat(dk[j], tt + dsn[j]);
+                                xa[2 * j + 1] = xat(dk[j], tt + dso[j]);
+                            }
+                    }
+                }
+            };
+            fetch(lane);
 #pragma unroll 1
             for (int t0 = 0; t0 < L; t0 += 32) {
                 const int t = t0 + lane;
+                float xc[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) xc[j] = xa[j];
+                fetch(t + 32);
                 float d = 0.0f;
                 if (first) {
                     if (t < L) {
-                        // every subband's load issued before the sum (in subband order)
+                        // subbands in order: the fetched 16, then any beyond
 #pragma unroll
-                        for (int kk = 0; kk < kMaxSub; kk += 16) {
-                            if (kk >= n_sub) break;
-                            float xv[16];
-#pragma unroll
-                            for (int j = 0; j < 16; ++j) xv[j] = (kk + j < n_sub) ? xat(kk + j, t + sh[kk + j]) : 0.0f;
-#pragma unroll
-                            for (int j = 0; j < 16; ++j)
-                                if (kk + j < n_sub) d += xv[j];
-                        }
+                        for (int j = 0; j < 16; ++j)
+                            if (j < n_sub) d += xc[j];
+#pragma unroll 1
+                        for (int k = 16; k < n_sub; ++k) d += xat(k, t + sh[k]);
                     }
                 } else {
                     const float oh = Pw[t + 1], ol = __half2float(Plo[t + 1]);
@@ -207,22 +238,14 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel_long(const __grid_c
                     pl_prev = __shfl_sync(kFull, ol, 31);
                     d = (oh - ph) + (ol - pl);
                     if (t < L) {
+#pragma unroll
+                        for (int j = 0; j < 2; ++j)
+                            if (j < nd) d = (d + xc[2 * j]) - xc[2 * j + 1];
 #pragma unroll 1
-                        for (int e0 = 0; e0 < nd; e0 += 2) {
-                            float xn[2], xo[2];
-#pragma unroll
-                            for (int j = 0; j < 2; ++j) {
-                                xn[j] = xo[j] = 0.0f;
-                                if (e0 + j < nd) {
-                                    const uint32_t pk = static_cast<uint32_t>(s_delta[d0 + e0 + j]);
-                                    const int k = pk & 63u, so = (pk >> 6) & 0x1fffu, sn = pk >> 19;
-                                    xn[j] = xat(k, t + sn);
-                                    xo[j] = xat(k, t + so);
-                                }
-                            }
-#pragma unroll
-                            for (int j = 0; j < 2; ++j)
-                                if (e0 + j < nd) d = (d + xn[j]) - xo[j];
+                        for (int e = 2; e < nd; ++e) {
+                            const uint32_t pk = static_cast<uint32_t>(s_delta[d0 + e]);
+                            const int k = pk & 63u, so = (pk >> 6) & 0x1fffu, sn = pk >> 19;
+                            d = (d + xat(k, t + sn)) - xat(k, t + so);
                         }
                     } else {
                         d = 0.0f;
@@ -334,11 +357,25 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel_long(const __grid_c
 
 }  // namespace dev
 
-// Warps per CTA of the long-window kernel: as many as the P rows allow, up to kWarps.
+// Warps per CTA of the long-window kernel.  The CTA waits for its slowest warp at every pixel, so
+// of the counts whose prefix rows fit, the one that completes the most DM rows per round
+// (n_rows / ceil(n_rows / warps)), the fewest warps on ties.
 int long_warps(const SearchParams &p, int max_smem) {
-    for (int w = kWarps; w >= 1; --w)
-        if (dev::long_layout(p, w).total <= static_cast<size_t>(max_smem)) return w;
-    return 0;
+    int fit = 0;
+    for (int w = kWarps; w >= 1 && fit == 0; --w)
+        if (dev::long_layout(p, w).total <= static_cast<size_t>(max_smem)) fit = w;
+    if (fit == 0) return 0;
+    const int n = p.n_u_active > 0 ? p.n_u_active : 1;
+    int best = 1;
+    double best_rate = 0.0;
+    for (int w = 1; w <= fit; ++w) {
+        const double rate = static_cast<double>(n) / ((n + w - 1) / w);
+        if (rate > best_rate + 1e-9) {
+            best_rate = rate;
+            best = w;
+        }
+    }
+    return best;
 }
 
 size_t long_smem(const SearchParams &p, int n_warps) { return dev::long_layout(p, n_warps).total; }
