@@ -249,3 +249,17 @@ def test_long_window_static_search(native):
                                         ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert st == native.EINVAL
     pm.close()
+
+
+@pytest.mark.parametrize("n_sub", [5, 24])
+def test_long_window_subband_counts(native, n_sub):
+    """Subband counts other than 16 (first rows read past the first 16 subbands; few subbands)."""
+    rng = np.random.default_rng(n_sub)
+    n_t = 1500
+    cfg = synth.SearchConfig(ny=3, nx=4, n_sub=n_sub, n_t=n_t, freq_mhz=synth.band_centres(n_sub),
+                             dm=np.sort(rng.uniform(0, 4000, 17)),
+                             widths=np.array([1, 2, 5, 16, 64, 300, 1024, 1500], np.int32), threshold=4.0)
+    cube = torch.from_numpy(rng.standard_normal((cfg.n_pix, n_sub, n_t)).astype(np.float32))
+    cube[5, :, 700:740] += 1.0
+    sig = np.full(cfg.n_pix, math.sqrt(n_sub), np.float32)
+    _check_full(native, cfg, cube, sig)
