@@ -341,7 +341,8 @@ def _serving_fields(native, synth, seed):
 
 def serving_latency(native, synth, n_blocks: int, paced_blocks: int, seed: int = 0):
     """Four concurrent fields (one plan, stream and CUDA graph each), BF16 window of 1200 samples
-    with re-scoring from the pinned FP32 window, 25-sample blocks from pinned host memory:
+    with re-scoring from the FP32 window (device memory where it fits), 25-sample blocks from pinned
+    host memory:
     push -> candidates device latency, unpaced (back to back) and paced (one block per field every
     3.355 s)."""
     import torch
@@ -367,7 +368,9 @@ def serving_latency(native, synth, n_blocks: int, paced_blocks: int, seed: int =
     lat, wall = run(n_blocks, False)
     lat = lat[2 * len(fields):]                     # the first two blocks of each field are warm-up
     out = {"fields": [f"{ny}x{nx}" for ny, nx in SERVING_FIELDS], "storage": "bf16",
-           "rescore_eps": SERVING_EPS, "rescore_from": "pinned host FP32 window", "block_samples": 25,
+           "rescore_eps": SERVING_EPS,
+           "rescore_from": ", ".join(sorted({{1: "device FP32 window", 2: "pinned host FP32 window"}.get(
+               plan.stream_window_info(), "none") for _, plan in fields})), "block_samples": 25,
            "window_samples": 1200, "blocks_per_field": n_blocks, "paced": False,
            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
            "max_ms": float(lat.max()), "blocks_per_s": 4 * n_blocks / wall, "cadence_s": CADENCE_S}

@@ -86,7 +86,8 @@ typedef struct {
                                 +-rescore_eps of the threshold are searched
                                 again in FP32 (offline: from the FP32 cube
                                 passed to nsfrb_search; serving: from an FP32
-                                copy of the window in pinned host memory);
+                                copy of the window, in device memory or, where
+                                that does not fit, pinned host memory);
                                 <= 0 disables re-scoring.  Measured BF16 S/N
                                 errors against the FP64 search of the FP32
                                 input: <= 0.03 with known noise (full-window
@@ -296,22 +297,32 @@ nsfrb_status nsfrb_search_static(nsfrb_plan_t plan, const void *d_cube, const fl
  * search runs as a captured CUDA graph.  Subbands missing from
  * present_mask are zero-filled for that block.
  * Re-scoring (16-bit storage with cfg.rescore_eps > 0): the stream also keeps
- * the window in FP32 in pinned host memory (ny*nx*n_sub*n_t*4 bytes, mapped,
- * written by the device as blocks arrive, sample plane by sample plane in the
- * block's [n_sub][ny][nx] layout); after each block the pixels whose
+ * the window in FP32 (ny*nx*n_sub*n_t*4 bytes, written by the device as blocks
+ * arrive, sample plane by sample plane in the block's [n_sub][ny][nx] layout):
+ * in device memory when the free device memory measured at admission covers
+ * the stream's bytes (nsfrb_stream_bytes), the window and hbm_reserve;
+ * otherwise in pinned, mapped host memory (written and read over the host
+ * link).  After each block the pixels whose
  * best S/N over the new trials lies within +-rescore_eps of the threshold are
  * searched again from it in FP32 (same new-trial mask) before the candidate
  * list is formed. */
 
 /* Admit a stream: allocates the window and block buffers if the device has
- * hbm_budget bytes free beyond what this stream needs (ENOMEM otherwise;
- * also ENOMEM if the pinned host window for re-scoring cannot be had).
+ * hbm_reserve bytes free beyond what this stream needs (ENOMEM otherwise;
+ * also ENOMEM if the re-score window fits neither the device nor pinned host
+ * memory).
  * n_blk: samples per block (1..n_t).  One plan serves one field; concurrent
  * fields are separate plans (each with its own stream and graph). */
 nsfrb_status nsfrb_stream_open(nsfrb_plan_t plan, int32_t n_blk, size_t hbm_reserve);
 
-/* Bytes of device memory a stream of this plan needs. */
+/* Bytes of device memory a stream of this plan needs (without the re-score
+ * FP32 window, which goes to the device only if it also fits). */
 nsfrb_status nsfrb_stream_bytes(nsfrb_plan_t plan, int32_t n_blk, size_t *bytes);
+
+/* Where the open stream keeps its re-score FP32 window: *fp32_window = 1 in
+ * device memory, 2 in pinned host memory, 0 no window (no re-scoring).
+ * ENOTREADY without an open stream. */
+nsfrb_status nsfrb_stream_window_info(nsfrb_plan_t plan, int32_t *fp32_window);
 
 /* Queue one block (asynchronous; h_block must stay valid until the next
  * nsfrb_stream_poll returns).  ENOTREADY if the previous block has not been

@@ -61,8 +61,10 @@ struct nsfrb_plan_s {
     void *d_ring = nullptr;
     float *d_blk = nullptr;        // [n_blk][n_sub][n_pix] FP32 block on the device
     int32_t *d_sstate = nullptr;   // [0] window start in the ring row, [1] samples written mod n_t
-    float *h_fring = nullptr;      // re-score: host-pinned FP32 window [n_t][n_sub][n_pix], a ring of
-    float *d_fring = nullptr;      //   n_t sample planes (mapped; d_fring is its device address)
+    float *h_fring = nullptr;      // re-score: FP32 window [n_t][n_sub][n_pix], a ring of n_t sample
+    float *d_fring = nullptr;      //   planes: in device memory (d_fring, h_fring null) when the
+    bool fring_dev = false;        //   admission budget allows, else pinned host memory (h_fring,
+                                   //   mapped; d_fring its device address)
     cudaStream_t s_stream = nullptr;
     cudaGraphExec_t s_graph = nullptr;
     cudaEvent_t s_ev_push = nullptr, s_ev_done = nullptr;

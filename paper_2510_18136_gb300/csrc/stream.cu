@@ -39,8 +39,8 @@ constexpr int kTrPix = 32;   // pixels per transpose tile
 // bit is clear in *mask are written as zero.  One CTA per (32-pixel tile,
 // subband); the tile is staged through shared memory so that both the reads
 // (along pixels) and the writes (along samples) are contiguous.  With fring
-// (re-score of 16-bit windows) the FP32 values also go to the host-pinned
-// window [n_t][n_sub][n_pix], a ring of n_t sample planes in the block's own
+// (re-score of 16-bit windows) the FP32 values also go to the FP32 window
+// [n_t][n_sub][n_pix] (device or pinned host memory), a ring of n_t sample planes in the block's own
 // layout, so that those writes are contiguous along pixels too.
 template <typename T>
 __global__ void ingest_kernel(const float *__restrict__ blk, T *__restrict__ ring, int64_t n_pix, int n_sub,
@@ -99,8 +99,10 @@ void destroy_stream_state(nsfrb_plan_s *pl) {
     cudaFree(pl->d_blk);
     cudaFree(pl->d_sstate);
     if (pl->h_fring) cudaFreeHost(pl->h_fring);
+    if (pl->fring_dev) cudaFree(pl->d_fring);
     pl->h_fring = nullptr;
     pl->d_fring = nullptr;
+    pl->fring_dev = false;
     pl->streaming = false;
     cudaGetLastError();
 }
@@ -124,6 +126,13 @@ nsfrb_status nsfrb_stream_bytes(nsfrb_plan_t plan, int32_t n_blk, size_t *bytes)
     const size_t blk = static_cast<size_t>(n_blk) * c.n_sub * n_pix * sizeof(float);
     const size_t work = n_pix * (sizeof(PixRec) + sizeof(CandRec) + sizeof(int32_t));
     *bytes = ring + blk + work + 4096;
+    return NSFRB_OK;
+}
+
+nsfrb_status nsfrb_stream_window_info(nsfrb_plan_t plan, int32_t *fp32_window) {
+    if (!plan || !fp32_window) return fail(plan, NSFRB_EINVAL, "null argument");
+    if (!plan->streaming) return fail(plan, NSFRB_ENOTREADY, "no open stream");
+    *fp32_window = plan->fring_dev ? 1 : (plan->h_fring ? 2 : 0);
     return NSFRB_OK;
 }
 
@@ -157,10 +166,24 @@ nsfrb_status nsfrb_stream_open(nsfrb_plan_t plan, int32_t n_blk, size_t hbm_rese
     }
     plan->streaming = true;
     plan->d_mask = reinterpret_cast<uint32_t *>(plan->d_sstate + 4);
-    // re-score of 16-bit windows: the FP32 window in pinned host memory, written by the
-    // ingest kernel and read back only for the pixels near the threshold
+    // re-score of 16-bit windows: the FP32 window, written by the ingest kernel and read back only
+    // for the pixels near the threshold; in device memory if the free memory measured for the
+    // admission also covers it beyond hbm_reserve (the ingest then writes it at HBM speed), else
+    // in pinned host memory over the host link
     const bool rescore = c.dtype != NSFRB_F32 && c.rescore_eps > 0.0f;
     if (rescore) {
+        const size_t fbytes = static_cast<size_t>(n_pix) * c.n_sub * c.n_t * sizeof(float);
+        if (free_b >= need + fbytes + hbm_reserve &&
+            cudaMalloc(reinterpret_cast<void **>(&plan->d_fring), fbytes) == cudaSuccess) {
+            plan->fring_dev = true;
+            if ((st = cuda_check(plan, cudaMemset(plan->d_fring, 0, fbytes), "FP32 window clear"))) {
+                destroy_stream_state(plan);
+                return st;
+            }
+        }
+        cudaGetLastError();
+    }
+    if (rescore && !plan->fring_dev) {
         const size_t fbytes = static_cast<size_t>(n_pix) * c.n_sub * c.n_t * sizeof(float);
         if (cudaHostAlloc(reinterpret_cast<void **>(&plan->h_fring), fbytes, cudaHostAllocMapped) != cudaSuccess) {
             cudaGetLastError();
@@ -216,7 +239,7 @@ nsfrb_status nsfrb_stream_open(nsfrb_plan_t plan, int32_t n_blk, size_t hbm_rese
                           n_blk, s, plan->d_sstate);
     if (ok && qs == NSFRB_OK && rescore) {
         // pixels whose best over the new trials lies within +-rescore_eps of the threshold:
-        // the same masked search again on their FP32 window rows, read from host memory
+        // the same masked search again on their FP32 window rows (device or host memory)
         qs = cuda_check(plan,
                         launch_rescore_select(plan->d_rec, n_pix, c.threshold, c.rescore_eps, plan->d_list,
                                               plan->d_nlist, s),

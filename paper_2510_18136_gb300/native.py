@@ -91,6 +91,7 @@ def _load() -> ctypes.CDLL:
         "nsfrb_stream_push": ([P, P, c_uint32], c_int32),
         "nsfrb_stream_poll": ([P, c_int32, P, c_int32, POINTER(c_int32), POINTER(c_float)], c_int32),
         "nsfrb_stream_blocks": ([P, POINTER(c_int64)], c_int32),
+        "nsfrb_stream_window_info": ([P, POINTER(c_int32)], c_int32),
         "nsfrb_stream_block": ([P, POINTER(c_void_p)], c_int32),
         "nsfrb_stream_push_device": ([P, c_uint32, P], c_int32),
         "nsfrb_imager_create": ([POINTER(nsfrb_imager_config), POINTER(c_void_p)], c_int32),
@@ -311,6 +312,13 @@ class Plan:
         _check(lib.nsfrb_stream_poll(self._h, int(timeout_ms), out.ctypes.data_as(c_void_p), cap,
                                      ctypes.byref(n), ctypes.byref(lat)), "nsfrb_stream_poll")
         return out[: n.value], float(lat.value)
+
+    def stream_window_info(self) -> int:
+        """``nsfrb_stream_window_info``: 1 re-score FP32 window in device memory, 2 in pinned host
+        memory, 0 none."""
+        v = c_int32()
+        _check(lib.nsfrb_stream_window_info(self._h, ctypes.byref(v)), "nsfrb_stream_window_info")
+        return int(v.value)
 
     def stream_blocks(self) -> int:
         n = c_int64()

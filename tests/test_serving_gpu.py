@@ -123,12 +123,14 @@ def test_stream_admission_and_protocol_errors(native):
     plan.close()
 
 
-@pytest.mark.parametrize("n_blk", [12, 25])
-def test_stream_bf16_rescore_from_fp32_window(native, n_blk):
-    """BF16 window with re-scoring from the pinned FP32 window: pixels whose best over the new
-    trials lies within eps of the threshold carry the FP32 result (FP64 oracle of the FP32
-    values within the FP32 tolerance), the rest the BF16 one, and the candidate set is the FP32
-    oracle's.  A block with a missing subband checks that the FP32 window is zero-filled too."""
+@pytest.mark.parametrize("n_blk,where", [(12, "device"), (25, "device"), (25, "host")])
+def test_stream_bf16_rescore_from_fp32_window(native, n_blk, where):
+    """BF16 window with re-scoring from the FP32 window: pixels whose best over the new trials
+    lies within eps of the threshold carry the FP32 result (FP64 oracle of the FP32 values within
+    the FP32 tolerance), the rest the BF16 one, and the candidate set is the FP32 oracle's.  A
+    block with a missing subband checks that the FP32 window is zero-filled too.  The window sits
+    in device memory when the admission budget allows, else in pinned host memory: a reserve that
+    leaves room for the ring but not the window forces the host placement."""
     cfg = synth.SearchConfig(ny=6, nx=7, n_t=96, dm=np.linspace(0, 1500, 20),
                              widths=np.array([1, 2, 4, 8, 16, 32, 50], np.int32), threshold=5.0)
     eps = 1.0
@@ -137,7 +139,15 @@ def test_stream_bf16_rescore_from_fp32_window(native, n_blk):
     seen = xn.copy()
     tab = oracle.delay_table(cfg.freq_mhz, cfg.dm)
     plan = native.Plan(cfg, dtype="bf16", rescore_eps=eps)
-    plan.stream_open(n_blk)
+    reserve = 0
+    if where == "host":
+        plan.search(torch.zeros((cfg.n_pix, cfg.n_sub, cfg.n_t), dtype=torch.bfloat16, device="cuda"))
+        plan.candidates()                              # the plan's device state exists from here on
+        free0 = torch.cuda.mem_get_info()[0]
+        fbytes = cfg.n_pix * cfg.n_sub * cfg.n_t * 4
+        reserve = free0 - plan.stream_bytes(n_blk) - fbytes // 2
+    plan.stream_open(n_blk, hbm_reserve=reserve)
+    assert plan.stream_window_info() == (1 if where == "device" else 2)
     n_rescored = 0
     for b in range(n_blocks):
         mask = (1 << 16) - 1
