@@ -207,19 +207,26 @@ def dataset(n_target: int, seed: int, cfg=None, device="cuda", balance: bool = T
     return x.contiguous(), torch.from_numpy(y.astype(np.float32)).to(device), k
 
 
-def train(clf: native.Classifier, x: torch.Tensor, y: torch.Tensor, epochs: int, seed: int = 0):
-    """Mini-batch training (shuffled each epoch); returns the per-epoch mean losses."""
+def train(clf: native.Classifier, x: torch.Tensor, y: torch.Tensor, epochs: int, seed: int = 0,
+          loss_every: int = 1):
+    """Mini-batch training (shuffled each epoch); returns the per-epoch mean losses.  The loss is
+    read back (a wait for the step) every loss_every steps and at the last step of an epoch, and
+    each epoch's mean is over the steps read; the other steps queue without waiting."""
     g = torch.Generator(device="cpu").manual_seed(seed)
     B = clf.batch
     n = x.shape[0] // B * B
     losses = []
     for _ in range(epochs):
         perm = torch.randperm(x.shape[0], generator=g)[:n].to(x.device)
-        tot = 0.0
-        for i in range(0, n, B):
+        tot, n_read = 0.0, 0
+        for j, i in enumerate(range(0, n, B)):
             idx = perm[i:i + B]
-            tot += clf.train_step(x[idx].contiguous(), y[idx].contiguous())
-        losses.append(tot / (n // B))
+            want = (j + 1) % loss_every == 0 or i + B >= n
+            loss = clf.train_step(x[idx].contiguous(), y[idx].contiguous(), want_loss=want)
+            if want:
+                tot += loss
+                n_read += 1
+        losses.append(tot / max(1, n_read))
     return losses
 
 
