@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel_long(const __grid_c
     const int32_t *s_shift = s_table + p.n_u * kInfo + p.n_deltas;
     float *Pw = s_pbuf + (size_t)warp * long_ppitch(n_t);
     __half *Plo = reinterpret_cast<__half *>(smem + lay.plo) + (size_t)warp * long_ppitch(n_t);
-    const size_t es = (ST == 0) ? 4 : 2;
+    constexpr size_t es = (ST == 0) ? 4 : 2;   // bytes per stored sample (pixel-major layouts)
     if (lane == 0) {
         Pw[0] = 0.0f;
         Plo[0] = __float2half_rn(0.0f);
@@ -146,9 +146,12 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel_long(const __grid_c
             s_inv[tid] = 1.0f / (sg * sqrtf(static_cast<float>(p.widths[tid])));
         }
         const bool bad = p.bad_pix && p.bad_pix[pix];
-        // the pixel's tile (plain layouts): subband k, window sample t at element k row_len + t_off + t
-        const void *tile = static_cast<const unsigned char *>(p.cube) +
-                           static_cast<size_t>(pix - p.cube_pix0) * n_sub * p.row_len * es;
+        // the pixel's tile (pixel-major layouts): subband k, window sample t at element
+        // k row_len + t_off + t
+        const void *tile = nullptr;
+        if constexpr (ST >= 0)
+            tile = static_cast<const unsigned char *>(p.cube) +
+                   static_cast<size_t>(pix - p.cube_pix0) * n_sub * p.row_len * es;
         __syncthreads();
 
         float bsnr = neg_inf();
