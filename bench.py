@@ -59,8 +59,9 @@ def parse():
                     help="blocks per field pushed at the 3.355 s cadence (0: skip)")
     ap.add_argument("--bf16-steps", type=int, default=5,
                     help="timed BF16 searches of the bench cube, with and without re-score (0: skip)")
-    ap.add_argument("--classifier-samples", type=int, default=24000,
-                    help="cutouts made on the fly and trained on once each in the classifier section (0: skip)")
+    ap.add_argument("--classifier-samples", type=int, default=200000,
+                    help="cutouts made on the fly and trained on once each in the classifier section (the "
+                         "classifier workload's 200k; 0: skip)")
     ap.add_argument("--classifier-eval-cubes", type=int, default=60,
                     help="fresh cubes the trained classifier is scored on")
     ap.add_argument("--campaigns", type=int, default=1,

@@ -106,10 +106,13 @@ def make_cube(cfg: synth.SearchConfig, seed: int, device="cuda", snr=(6.0, 30.0)
             continue
         span = max(cfg.n_t - int(smax[i]) - ws[i], 1)
         t0s[i] = int(rng.integers(0, span))
-    # vectorised injection: (pixel, subband, sample, amplitude) entries added by one index_put
-    idx_p, idx_k, idx_t, val = [], [], [], []
+    # injection: per source its spatial taps (pixel, weight) and its valid (subband, sample) cells;
+    # every (tap, cell) pair of a source is one entry of the cube, built on the device from the
+    # concatenated tables and added by one index_add
+    taps_p, taps_a, cells, n_cell = [], [], [], []
     psf_dy, psf_dx = np.meshgrid(np.arange(5) - 2, np.arange(5) - 2, indexing="ij")
     psf_taps = (psf_dy.ravel(), psf_dx.ravel(), psf.ravel())
+    plane = cfg.n_sub * cfg.n_t
     for i, kind in enumerate(kinds):
         w = ws[i]
         if kind == KIND_SPIKE:
@@ -130,19 +133,26 @@ def make_cube(cfg: synth.SearchConfig, seed: int, device="cuda", snr=(6.0, 30.0)
             dy, dx, wt = psf_taps
         pix = ((rows[i] + dy) % cfg.ny) * cfg.nx + (cols[i] + dx) % cfg.nx          # [taps]
         t = t0s[i] + sh[i][k_sel][:, None] + np.arange(w)[None, :]                   # [k, w]
-        ok = t < cfg.n_t
-        P = np.broadcast_to(pix[:, None, None], (pix.size,) + t.shape)
-        K = np.broadcast_to(k_sel[None, :, None], P.shape)
-        T = np.broadcast_to(t[None], P.shape)
-        V = np.broadcast_to((amp * wt)[:, None, None], P.shape)
-        m = np.broadcast_to(ok[None], P.shape)
-        idx_p.append(P[m]); idx_k.append(K[m]); idx_t.append(T[m]); val.append(V[m].astype(np.float32))
-    if idx_p:
-        ip = torch.from_numpy(np.concatenate(idx_p)).to(device)
-        ik = torch.from_numpy(np.concatenate(idx_k)).to(device)
-        it = torch.from_numpy(np.concatenate(idx_t)).to(device)
-        vv = torch.from_numpy(np.concatenate(val)).to(device)
-        cube.index_put_((ip, ik, it), vv, accumulate=True)
+        kk, ww = np.nonzero(t < cfg.n_t)
+        c = k_sel[kk] * cfg.n_t + t[kk, ww]                                          # [valid (k, t)]
+        taps_p.append(pix.astype(np.int64) * plane)
+        taps_a.append((amp * wt).astype(np.float32))
+        cells.append(c.astype(np.int64))
+        n_cell.append(np.full(pix.size, c.size, np.int64))
+    if taps_p:
+        tp = torch.from_numpy(np.concatenate(taps_p)).to(device)     # [taps of all sources]
+        ta = torch.from_numpy(np.concatenate(taps_a)).to(device)
+        nc = np.concatenate(n_cell)                                   # cells of each tap's source
+        # first cell of each tap's source in the concatenated cell table
+        starts = np.cumsum([0] + [x.size for x in cells[:-1]])
+        c0 = np.concatenate([np.full(x.size, st, np.int64) for x, st in zip(taps_p, starts)])
+        cl = torch.from_numpy(np.concatenate(cells)).to(device)
+        ncd = torch.from_numpy(nc).to(device)
+        n_ent = int(nc.sum())
+        tap_of = torch.repeat_interleave(torch.arange(tp.numel(), device=device), ncd, output_size=n_ent)
+        seg0 = torch.cumsum(ncd, 0) - ncd                             # first entry of each tap
+        cell = torch.arange(n_ent, device=device) - seg0[tap_of] + torch.from_numpy(c0).to(device)[tap_of]
+        cube.view(-1).index_add_(0, tp[tap_of] + cl[cell], ta[tap_of])
     truth = Truth(kind=np.array(kinds), row=np.array(rows), col=np.array(cols), t0=np.array(t0s),
                   width=np.array(ws), dm=dms, snr=np.array(snrs))
     return cube, truth
