@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16"])
+    ap.add_argument("--out", default="candidates", choices=["candidates", "full"],
+                    help="full: also S/N and TOA for every (pixel, DM, width) on the device")
     ap.add_argument("--ny", type=int, default=301)
     ap.add_argument("--nx", type=int, default=301)
     ap.add_argument("--n-t", type=int, default=1200,
@@ -148,7 +150,7 @@ def measured_traffic(ny, nx, dtype):
     return NCU_TRAFFIC["bytes"]
 
 
-def search_kernel_name(n_t, dtype, noise="known", tile=None):
+def search_kernel_name(n_t, dtype, noise="known", tile=None, out="candidates"):
     """The kernels the library launches for this window: chunks of C samples per lane, the smallest
     compiled C with 32 C > n_t.  With known noise the barrier-free kernel runs (FP32 rows; 16-bit
     rows read in place when C is even and the rows fill whole 16-byte units), with the pixel x DM
@@ -158,6 +160,8 @@ def search_kernel_name(n_t, dtype, noise="known", tile=None):
     if n_t > 1247:   # beyond the register path: the long-window kernel (MAD slabs are FP32)
         return f"search_kernel_long<{0 if noise == 'mad' else st}, false>"
     c = next(c for c in (1, 3, 5, 9, 17, 25, 38, 39) if 32 * c >= n_t + 1)
+    if out == "full":
+        return f"search_kernel<{c}, true>"
     tt = "" if tile is None else f", {int(tile) // 10}, {int(tile) % 10}"
     if noise == "mad":
         return f"mad_normalise_kernel + search_kernel_pipe<{c}, 0{tt}> (FP32 slabs)"
@@ -789,13 +793,15 @@ def main():
     cfg.sigma_pix = synth.psf_sigma()
     cube, inj = make_cube(native, synth, cfg, args.seed + rank, dev, args.dtype)
     sigma = torch.full((cfg.n_pix,), cfg.sigma_pix * math.sqrt(cfg.n_sub), device=dev)
-    plan = native.Plan(cfg, dtype=args.dtype)
+    plan = native.Plan(cfg, dtype=args.dtype, out=args.out)
     stream = torch.cuda.current_stream()
     # pixel x DM tile of the search kernel: each tile that fits timed on this cube, the fastest kept
     tile, tile_ms = plan.autotune(cube, sigma, reps=3, stream=stream)
     ops, n_unique = alg_ops(cfg, plan)
     elem = 4 if args.dtype == "f32" else 2
     alg_bytes = cfg.n_pix * cfg.n_sub * cfg.n_t * elem + cfg.n_pix * 4 + cfg.n_pix * 16
+    if args.out == "full":   # S/N (f32) and TOA (i16) of every (pixel, DM, width)
+        alg_bytes += cfg.n_pix * len(cfg.dm) * len(cfg.widths) * 6
 
     # N ranks: the image is N 301-row bands (shard.row_bands of an (N ny) x nx field), one per GPU,
     # each band's candidates gathered to rank 0 and merged in pixel order every step (weak scaling)
@@ -895,7 +901,8 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
         "config": {"workload": workload_name(cfg), "ny": cfg.ny, "nx": cfg.nx, "n_sub": cfg.n_sub, "n_t": cfg.n_t,
                    "n_dm": len(cfg.dm), "n_unique_dm_rows": n_unique, "widths": [int(w) for w in cfg.widths],
-                   "storage": args.dtype, "noise": "known sigma", "l2": "inputs larger than L2 (cube "
+                   "storage": args.dtype, "noise": "known sigma", "output": args.out,
+                   "l2": "inputs larger than L2 (cube "
                    f"{alg_bytes / 1e9:.2f} GB)",
                    "parallelism": (f"row bands x{world}: a {cfg.ny * world}x{cfg.nx} image, one {cfg.ny}-row band "
                                    "per GPU, candidate lists gathered to rank 0 each step" if world > 1 else
@@ -903,7 +910,7 @@ def main():
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                      "unit": "TFLOP/s", "frac": achieved / peak_ops,
                      "traffic": measured_traffic(cfg.ny, cfg.nx, args.dtype),
-                     "kernel": search_kernel_name(cfg.n_t, args.dtype, tile=tile),
+                     "kernel": search_kernel_name(cfg.n_t, args.dtype, tile=tile, out=args.out),
                      "kernel_ms": kern_s * 1e3, "tile": tile, "tile_ms": tile_ms,
                      "ops_per_launch": ops, "peak_basis": f"{n_sm} SM x 128 FP32 lanes x "
                      f"{pk['sm_max_mhz']:.0f} MHz ({pk['source']} max clock)"},

@@ -107,8 +107,12 @@ struct SearchParams {
 
 // Shared-memory carve-up, identical on host and device.
 struct SmemLayout {
-    size_t table, xs, stg, pbuf, hist, wbest, sinv, bar, total;
+    size_t table, xs, stg, pbuf, fscr, hist, wbest, sinv, bar, total;
 };
+
+// Floats per warp of the earliest-sample search's scratch (a lane's extended in-lane prefix:
+// C + 16 values for the sample-pair chunk C = 38).
+constexpr int kFindScr = 64;
 
 __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -127,6 +131,8 @@ __host__ __device__ inline SmemLayout smem_layout(const SearchParams &p, int C) 
     if (p.stage == 2) o += align_up((size_t)2 * p.n_sub * p.stg_pitch, 128);
     L.pbuf = o;
     o += sizeof(float) * (size_t)kWarps * 32 * C;
+    L.fscr = o;
+    if (C % 2 == 0) o += sizeof(float) * (size_t)kWarps * kFindScr;
     L.hist = o;
     // MAD histograms: in the staging buffer of the current item when staging, else own space
     if (p.noise_mode == 1 && p.stage != 2) o += sizeof(uint32_t) * (size_t)kWarps * kHistBins;

@@ -800,40 +800,116 @@ __device__ __forceinline__ float lane_carry(float tot, int lane) {
     return (lane == 0) ? 0.0f : carry;
 }
 
+// Earliest-sample searches for even chunks, by the whole warp on the trials of the lanes that hold
+// the target (match: their bits; found from the lanes' own maxima), with the operations of the
+// maximum pass; the result is the same on every lane.
+
+// In-lane width W (lane j's trials are samples j C .. j C + C - 1, lanes in sample order): the
+// lowest matching lane's extended prefix (D for W = 1) goes to the warp's scratch, and its C trials
+// are evaluated 32 at a time.
+template <int C, int SH, int W>
+__device__ __forceinline__ int small_find_coop(const float2 (&D)[C / 2], const float2 (&Lp)[C / 2],
+                                               const float2 (&Hh)[SH / 2], float *scr, unsigned match, int lane,
+                                               float inv, float target) {
+    static_assert(C + SH <= kFindScr, "scratch holds a lane's extended prefix");
+    const int src = __ffs(match) - 1;
+    __syncwarp();
+    if (lane == src) {
+        float2 *s2 = reinterpret_cast<float2 *>(scr);
+        if constexpr (W == 1) {
+#pragma unroll
+            for (int m = 0; m < C / 2; ++m) s2[m] = D[m];
+        } else {
+#pragma unroll
+            for (int m = 0; m < C / 2; ++m) s2[m] = Lp[m];
+#pragma unroll
+            for (int m = 0; m < SH / 2; ++m) s2[C / 2 + m] = Hh[m];
+        }
+    }
+    __syncwarp();
+    int found = INT_MAX;
+#pragma unroll
+    for (int c0 = 0; c0 < C; c0 += 32) {
+        const int c = c0 + lane;
+        bool hit = false;
+        if (c < C) {
+            const float b = (W == 1) ? scr[c] : scr[c + W] - scr[c];
+            hit = b * inv == target;
+        }
+        const unsigned bal = __ballot_sync(kFull, hit);
+        if (bal && found == INT_MAX) found = src * C + c0 + __ffs(bal) - 1;
+    }
+    return found;
+}
+
+template <int C, int SH>
+__device__ __forceinline__ int small_find_coop_w(int w, const float2 (&D)[C / 2], const float2 (&Lp)[C / 2],
+                                                 const float2 (&Hh)[SH / 2], float *scr, unsigned match, int lane,
+                                                 float inv, float target) {
+    switch (w) {
+        case 1: return small_find_coop<C, SH, 1>(D, Lp, Hh, scr, match, lane, inv, target);
+        case 2: if constexpr (2 <= SH) return small_find_coop<C, SH, 2>(D, Lp, Hh, scr, match, lane, inv, target); break;
+        case 4: if constexpr (4 <= SH) return small_find_coop<C, SH, 4>(D, Lp, Hh, scr, match, lane, inv, target); break;
+        case 8: if constexpr (8 <= SH) return small_find_coop<C, SH, 8>(D, Lp, Hh, scr, match, lane, inv, target); break;
+        case 16: if constexpr (16 <= SH) return small_find_coop<C, SH, 16>(D, Lp, Hh, scr, match, lane, inv, target); break;
+        default: break;
+    }
+    return INT_MAX;
+}
+
+// Lane-strided width 32 M (lane j's trials are samples 32 i + j, i < C - M, from P in shared
+// memory): each matching lane's trials evaluated by the warp, the earliest over the lanes kept.
+template <int C>
+__device__ __forceinline__ int large_find_coop(const float *Pw, int M, unsigned match, int lane, float inv,
+                                               float target) {
+    int best = INT_MAX;
+    while (match) {
+        const int j = __ffs(match) - 1;
+        match &= match - 1;
+        int found = INT_MAX;
+#pragma unroll
+        for (int k0 = 0; k0 < C; k0 += 32) {
+            const int k = k0 + lane;
+            const bool hit = k < C - M && (Pw[32 * (k + M) + j] - Pw[32 * k + j]) * inv == target;
+            const unsigned bal = __ballot_sync(kFull, hit);
+            if (bal && found == INT_MAX) found = 32 * (k0 + __ffs(bal) - 1) + j;
+        }
+        best = min(best, found);
+    }
+    return best;
+}
+
 // Even chunks: the earliest sample whose boxcar of width index wi reaches `target`, from the
 // row's D (in-lane widths) or its P in shared memory (lane-strided and generic widths),
-// evaluated with the operations of the maximum pass.  Returns the minimum over the warp.
+// evaluated with the operations of the maximum pass; match: the lanes whose own best is
+// (target, wi).  The same on every lane.
 template <int C>
 __device__ __forceinline__ int find_t_even(const SearchParams &p, const float2 (&D)[C / 2], const float *Pw, int wi,
-                                           float inv, float target, int L, int lane, bool masked) {
+                                           float inv, float target, int L, int lane, bool masked, unsigned match,
+                                           float *scr) {
     constexpr int SH = (C < kSmallMax) ? C : kSmallMax;
     const int w = p.widths[wi];
-    int t;
-    if (masked && p.new_blk <= 32) {
-        t = masked_find32(Pw, w, masked_end(L, p.new_blk, lane), inv, target);
-    } else if (masked || p.wclass[wi] == WC_GENERIC) {
+    if (masked && p.new_blk <= 32)
+        return warp_min(masked_find32(Pw, w, masked_end(L, p.new_blk, lane), inv, target));
+    if (masked || p.wclass[wi] == WC_GENERIC) {
         const int tl = masked ? max(0, L - w - p.new_blk + 1) : 0;
-        t = generic_find(Pw, w, L, tl, lane, inv, target);
-    } else if (p.wclass[wi] == WC_SMALL) {
+        return warp_min(generic_find(Pw, w, L, tl, lane, inv, target));
+    }
+    if (p.wclass[wi] == WC_SMALL) {
         float2 Lp[C / 2];
         float2 Hh[SH / 2];
         const float tot = prefix_pairs<C>(D, Lp);
         halo_pairs<C, SH>(Lp, tot, lane, Hh);
-        t = small_find_pk<C, SH>(w, D, Lp, Hh, inv, target, lane * C);
-    } else {
-        float Ps[C];
-#pragma unroll
-        for (int i = 0; i < C; ++i) Ps[i] = Pw[32 * i + lane];
-        t = large_find<C>(w >> 5, Ps, inv, target, lane);
+        return small_find_coop_w<C, SH>(w, D, Lp, Hh, scr, match, lane, inv, target);
     }
-    return warp_min(t);
+    return large_find_coop<C>(Pw, w >> 5, match, lane, inv, target);
 }
 
 // search_rows for even chunks (sample pairs, see above).  The pixel's rows are in storage ST
 // (0 FP32, 1 BF16, 2 FP16) with the window at element eoff of each row; with mask_tail the
 // elements past the window are not -inf and the de-dispersed samples past L are set to -inf.
 template <int C, bool FULL, int ST = 0, typename OnRead = NoReadDone>
-__device__ __forceinline__ PixRec search_rows_even(const SearchParams &p, const void *xs, float *Pw,
+__device__ __forceinline__ PixRec search_rows_even(const SearchParams &p, const void *xs, float *Pw, float *Sw,
                                                    const float *s_inv, const int32_t *s_info,
                                                    const int32_t *s_delta, const int32_t *s_shift, int u_lo,
                                                    int u_hi, int64_t pix, int lane, int eoff = 0,
@@ -900,7 +976,9 @@ __device__ __forceinline__ PixRec search_rows_even(const SearchParams &p, const 
             if (wi >= 0) {                                                                                \
                 const float mw = warp_max(m), sw = mw * s_inv[wi];                                       \
                 int t = INT_MAX;                                                                          \
-                if (mw != neg_inf()) t = warp_min(small_find_pk_w<C, SH, (1 << J)>(D, Lp, Hh, s_inv[wi], sw, t0)); \
+                if (mw != neg_inf())                                                                      \
+                    t = small_find_coop<C, SH, (1 << J)>(D, Lp, Hh, Sw, __ballot_sync(kFull, m * s_inv[wi] == sw), \
+                                                         lane, s_inv[wi], sw);                                   \
                 write_full(wi, sw, t);                                                                    \
             }                                                                                             \
         }                                                                                                 \
@@ -926,7 +1004,9 @@ __device__ __forceinline__ PixRec search_rows_even(const SearchParams &p, const 
             if (wi >= 0) {                                                                                \
                 const float mw = warp_max(m), sw = mw * s_inv[wi];                                       \
                 int t = INT_MAX;                                                                          \
-                if (mw != neg_inf()) t = find_t_even<C>(p, D, Pw, wi, s_inv[wi], sw, L, lane, false);    \
+                if (mw != neg_inf())                                                                      \
+                    t = large_find_coop<C>(Pw, (1 << J) >> 5, __ballot_sync(kFull, m * s_inv[wi] == sw), lane, \
+                                           s_inv[wi], sw);                                                       \
                 write_full(wi, sw, t);                                                                    \
             }                                                                                             \
         }                                                                                                 \
@@ -975,6 +1055,8 @@ __device__ __forceinline__ PixRec search_rows_even(const SearchParams &p, const 
 
         // warp arg-max over (S/N, width index), only when some lane beats the warp's best
         if (__any_sync(kFull, ls > bsnr)) {
+            const float ls_own = ls;
+            const int lw_own = lw;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 const float os = __shfl_xor_sync(kFull, ls, o);
@@ -985,8 +1067,10 @@ __device__ __forceinline__ PixRec search_rows_even(const SearchParams &p, const 
                 }
             }
             if (ls > bsnr) {
-                // earliest sample reaching this S/N, re-evaluated with the same operations
-                const int t = find_t_even<C>(p, D, Pw, lw, s_inv[lw], ls, L, lane, masked);
+                // earliest sample reaching this S/N, re-evaluated with the same operations on the
+                // lanes whose own best it is
+                const unsigned match = __ballot_sync(kFull, ls_own == ls && lw_own == lw);
+                const int t = find_t_even<C>(p, D, Pw, lw, s_inv[lw], ls, L, lane, masked, match, Sw);
                 bsnr = ls;
                 bu = u;
                 bwi = lw;
@@ -1000,13 +1084,14 @@ __device__ __forceinline__ PixRec search_rows_even(const SearchParams &p, const 
 
 // Per-warp row search for chunk size C (pairs for even C).  Odd chunks read FP32 rows only.
 template <int C, bool FULL, int ST = 0, typename OnRead = NoReadDone>
-__device__ __forceinline__ PixRec search_rows_any(const SearchParams &p, const void *xs, float *Pw, const float *s_inv,
+__device__ __forceinline__ PixRec search_rows_any(const SearchParams &p, const void *xs, float *Pw, float *Sw,
+                                                  const float *s_inv,
                                                   const int32_t *s_info, const int32_t *s_delta,
                                                   const int32_t *s_shift, int u_lo, int u_hi, int64_t pix,
                                                   int lane, int eoff = 0, bool mask_tail = false,
                                                   OnRead on_read = OnRead{}) {
     if constexpr (C % 2 == 0) {
-        return search_rows_even<C, FULL, ST, OnRead>(p, xs, Pw, s_inv, s_info, s_delta, s_shift, u_lo, u_hi, pix,
+        return search_rows_even<C, FULL, ST, OnRead>(p, xs, Pw, Sw, s_inv, s_info, s_delta, s_shift, u_lo, u_hi, pix,
                                                      lane, eoff, mask_tail, on_read);
     } else {
         static_assert(ST == 0, "odd chunks read FP32 rows");
@@ -1094,6 +1179,7 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel(const __grid_consta
     const int u_lo = (warp * n_ua) / kWarps;
     const int u_hi = ((warp + 1) * n_ua) / kWarps;
     float *Pw = s_pbuf + (size_t)warp * 32 * C;
+    float *Sw = reinterpret_cast<float *>(smem + lay.fscr) + (size_t)warp * kFindScr;
 
     uint32_t phase[2] = {0u, 0u};
     if (p.stage != 0 && tid == 0 && blockIdx.x < n_items) issue(blockIdx.x, 0);
@@ -1214,7 +1300,7 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel(const __grid_consta
         // ---- per-warp search over its rows
         PixRec wr{neg_inf(), -1, -1, -1};
         if (!bad_pixel)
-            wr = search_rows_any<C, FULL, 0>(p, xs, Pw, s_inv, s_info, s_delta, s_shift, u_lo, u_hi, pix, lane);
+            wr = search_rows_any<C, FULL, 0>(p, xs, Pw, Sw, s_inv, s_info, s_delta, s_shift, u_lo, u_hi, pix, lane);
         const float bsnr = wr.snr;
         const int bu = wr.dm_idx, bwi = wr.w_idx, bt = wr.t_idx;
         // FULL mode: DM rows that have no trial at all
@@ -1364,6 +1450,7 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel_pipe(const __grid_c
 
     const int n_ua = p.n_u_active;
     float *Pw = s_pbuf + (size_t)warp * 32 * C;
+    float *Sw = reinterpret_cast<float *>(smem + lay.fscr) + (size_t)warp * kFindScr;
     int issued_last = -1;   // local index of the last item whose copy this warp started
     int i = 0;
     for (int64_t it = it0; it < n_items; it += G, ++i) {
@@ -1405,10 +1492,10 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel_pipe(const __grid_c
         };
         PixRec wr;
         if constexpr (kEarly)
-            wr = search_rows_any<C, false, ST>(p, s_xs + sl * buf_bytes, Pw, s_inv + rs * kMaxW, s_info, s_delta,
+            wr = search_rows_any<C, false, ST>(p, s_xs + sl * buf_bytes, Pw, Sw, s_inv + rs * kMaxW, s_info, s_delta,
                                                s_shift, u_lo, u_hi, pix, lane, eoff, mask_tail, read_done);
         else
-            wr = search_rows_any<C, false, ST>(p, s_xs + sl * buf_bytes, Pw, s_inv + rs * kMaxW, s_info, s_delta,
+            wr = search_rows_any<C, false, ST>(p, s_xs + sl * buf_bytes, Pw, Sw, s_inv + rs * kMaxW, s_info, s_delta,
                                                s_shift, u_lo, u_hi, pix, lane, eoff, mask_tail);
         // publish; this warp's reads of buffer sl are done before the copy that refills it
         fence_proxy_async();
