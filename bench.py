@@ -123,7 +123,7 @@ def make_cube(native, synth, cfg, seed, device, dtype):
 # DRAM bytes (read + write) per 301x301 FP32 launch from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum of a 128x128 launch, 1262.8 MB, scaled by 90601 / 16384 pixels), valid for the
 # kernel source with this sha256 prefix.
-NCU_TRAFFIC = {"sha256_16": "532b740754aa5456", "bytes": 6.983e9, "workload": (301, 301, "f32")}
+NCU_TRAFFIC = {"sha256_16": "0a686c2380c238c8", "bytes": 6.978e9, "workload": (301, 301, "f32")}
 
 
 # DRAM bytes of one imager call (grid_kernel + transform_kernel) from the ncu launch list of the
@@ -154,20 +154,19 @@ def search_kernel_name(n_t, dtype, noise="known", tile=None, out="candidates"):
     """The kernels the library launches for this window: chunks of C samples per lane, the smallest
     compiled C with 32 C > n_t.  With known noise the barrier-free kernel runs (FP32 rows; 16-bit
     rows read in place when C is even and the rows fill whole 16-byte units), with the pixel x DM
-    tile (teams, buffers per team) the plan chose; MAD normalisation is a pass of its own into FP32
-    slabs that the barrier-free kernel then searches."""
+    tile (teams T, buffers per team B) the plan chose; MAD normalisation is a pass of its own into
+    FP32 slabs that the barrier-free kernel then searches.  The last template argument is FULL."""
     st = {"f32": 0, "bf16": 1, "f16": 2}[dtype]
+    full = 1 if out == "full" else 0     # bool template arguments as ncu prints them
     if n_t > 1247:   # beyond the register path: the long-window kernel (MAD slabs are FP32)
-        return f"search_kernel_long<{0 if noise == 'mad' else st}, false>"
+        return f"search_kernel_long<{0 if noise == 'mad' else st}, {full}>"
     c = next(c for c in (1, 3, 5, 9, 17, 25, 38, 39) if 32 * c >= n_t + 1)
-    if out == "full":
-        return f"search_kernel<{c}, true>"
-    tt = "" if tile is None else f", {int(tile) // 10}, {int(tile) % 10}"
+    tt = ", T, B" if tile is None else f", {int(tile) // 10}, {int(tile) % 10}"
     if noise == "mad":
-        return f"mad_normalise_kernel + search_kernel_pipe<{c}, 0{tt}> (FP32 slabs)"
+        return f"mad_normalise_kernel + search_kernel_pipe<{c}, 0{tt}, {full}> (FP32 slabs)"
     if st == 0 or (c % 2 == 0 and n_t % 8 == 0):
-        return f"search_kernel_pipe<{c}, {st}{tt}>"
-    return f"search_kernel<{c}, false>"
+        return f"search_kernel_pipe<{c}, {st}{tt}, {full}>"
+    return f"search_kernel<{c}, {full}>"
 
 
 def alg_ops(cfg, plan):
@@ -799,9 +798,11 @@ def main():
     tile, tile_ms = plan.autotune(cube, sigma, reps=3, stream=stream)
     ops, n_unique = alg_ops(cfg, plan)
     elem = 4 if args.dtype == "f32" else 2
-    alg_bytes = cfg.n_pix * cfg.n_sub * cfg.n_t * elem + cfg.n_pix * 4 + cfg.n_pix * 16
-    if args.out == "full":   # S/N (f32) and TOA (i16) of every (pixel, DM, width)
-        alg_bytes += cfg.n_pix * len(cfg.dm) * len(cfg.widths) * 6
+    cube_bytes = cfg.n_pix * cfg.n_sub * cfg.n_t * elem
+    full_bytes = cfg.n_pix * len(cfg.dm) * len(cfg.widths) * 6 if args.out == "full" else 0
+    # cube and sigma read, one 16-byte record per pixel written, and in FULL mode the S/N (f32) and
+    # TOA (i16) of every (pixel, DM, width)
+    alg_bytes = cube_bytes + cfg.n_pix * 4 + cfg.n_pix * 16 + full_bytes
 
     # N ranks: the image is N 301-row bands (shard.row_bands of an (N ny) x nx field), one per GPU,
     # each band's candidates gathered to rank 0 and merged in pixel order every step (weak scaling)
@@ -842,7 +843,8 @@ def main():
     elapsed_max = float(t.item())
     value = world * args.steps * cfg.n_trials / elapsed_max
 
-    # end to end: host cube (pinned) -> device -> search -> candidates back to the host
+    # end to end: host cube (pinned) -> device -> search -> candidates (and in FULL mode the FULL
+    # arrays) back to the host
     host_cube = cube.cpu().pin_memory()
     host_sigma = sigma.cpu().pin_memory()
     plan.search_host(host_cube, host_sigma, stream=stream)
@@ -855,6 +857,8 @@ def main():
     for _ in range(args.e2e_steps):
         plan.search_host(host_cube, host_sigma, stream=stream)
         n_c = len(plan.candidates())
+        if args.out == "full":
+            plan.full()
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_s = e0.elapsed_time(e1) / 1e3
@@ -903,7 +907,7 @@ def main():
                    "n_dm": len(cfg.dm), "n_unique_dm_rows": n_unique, "widths": [int(w) for w in cfg.widths],
                    "storage": args.dtype, "noise": "known sigma", "output": args.out,
                    "l2": "inputs larger than L2 (cube "
-                   f"{alg_bytes / 1e9:.2f} GB)",
+                   f"{cube_bytes / 1e9:.2f} GB)",
                    "parallelism": (f"row bands x{world}: a {cfg.ny * world}x{cfg.nx} image, one {cfg.ny}-row band "
                                    "per GPU, candidate lists gathered to rank 0 each step" if world > 1 else
                                    "one GPU")},
@@ -916,8 +920,8 @@ def main():
                      f"{pk['sm_max_mhz']:.0f} MHz ({pk['source']} max clock)"},
         "hbm": {"achieved_gbs": hbm_gbs, "peak_gbs": pk["hbm_gbs"], "frac": hbm_gbs / pk["hbm_gbs"],
                 "bytes_per_launch": alg_bytes, "peak_source": pk["source"]},
-        "e2e": {"value": e2e_value, "unit": "trials/s", "h2d_bytes_per_step": alg_bytes - cfg.n_pix * 16,
-                "d2h_bytes_per_step": 8 + 24 * n_c},
+        "e2e": {"value": e2e_value, "unit": "trials/s", "h2d_bytes_per_step": cube_bytes + cfg.n_pix * 4,
+                "d2h_bytes_per_step": 8 + 24 * n_c + full_bytes},
         "gpu_launches": 3 * args.steps,
         "candidates": int(len(cand)), "injections": int(len(inj)),
         "p99_block_latency_ms": None if serving is None else serving["p99_ms"],

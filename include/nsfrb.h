@@ -190,8 +190,8 @@ nsfrb_status nsfrb_plan_get_tile(nsfrb_plan_t plan, int32_t dtype, int32_t *tile
  * no re-score), `reps` timed searches each after one warm-up, and keep the
  * one with the smallest median search time as the plan's preference for the
  * storage type the kernel searched.  h_tile (or NULL) gets that tile (0 when
- * the plan's searches do not use this kernel: FULL output, MAD windows of
- * n_t not a multiple of 4, windows over 1247 samples); h_ms[NSFRB_N_TILES] (or NULL) the medians in
+ * the plan's searches do not use this kernel: MAD windows of n_t not a
+ * multiple of 4, windows over 1247 samples); h_ms[NSFRB_N_TILES] (or NULL) the medians in
  * NSFRB_TILES order, -1 for tiles that do not fit.  Synchronous: it waits
  * for every search it queues on `stream`.  Afterwards the plan's results are
  * those of one search of the cube with the chosen tile.  Errors: as

@@ -132,9 +132,10 @@ bool choose_stage_for(int C, int max_smem, SearchParams &sp, size_t &smem, int t
     const int n_t = sp.n_t;
     const int epv = 16 / static_cast<int>(elem_size(sp.dtype));   // samples per 16 bytes
     // The barrier-free kernel: rows bulk-copied as stored (FP32, or 16-bit read in place, which
-    // needs the sample-pair path of even chunks), KNOWN noise, per-pixel records only.  The copy
-    // starts at the 16-byte boundary at or below the window start and must stay inside the row.
-    if (sp.t_wrap == 0 && sp.t_stride == 0 && sp.noise_mode == 0 && !sp.full_snr &&
+    // needs the sample-pair path of even chunks), KNOWN noise (or MAD-normalised FP32 slabs), records
+    // and FULL arrays.  The copy starts at the 16-byte boundary at or below the window start and must
+    // stay inside the row.
+    if (sp.t_wrap == 0 && sp.t_stride == 0 && sp.noise_mode == 0 &&
         (sp.dtype == NSFRB_F32 || C % 2 == 0) &&
         base % 16 == 0 && sp.row_len % epv == 0) {
         bool fits_row;
@@ -297,8 +298,9 @@ nsfrb_status queue_search(nsfrb_plan_s *pl, const void *cube, int64_t cube_pix0,
 bool mad_slabs_apply(const nsfrb_plan_s *pl) {
     const nsfrb_config &c = pl->cfg;
     if (c.noise_mode != NSFRB_NOISE_MAD) return false;
-    // long windows: always (their kernel has no in-kernel selection), in either output mode
-    return pl->C == kLongC || (c.out_mode == NSFRB_OUT_CANDIDATES && c.n_t % 4 == 0);
+    // in either output mode; long windows always (their kernel has no in-kernel selection), other
+    // windows when the FP32 slab rows fill whole 16-byte units (the barrier-free kernel's copies)
+    return pl->C == kLongC || c.n_t % 4 == 0;
 }
 
 nsfrb_status queue_search_mad(nsfrb_plan_s *pl, const void *cube, int dtype, int64_t pix0, int64_t n,

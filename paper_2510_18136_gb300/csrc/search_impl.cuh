@@ -593,6 +593,21 @@ struct NoReadDone {
     __device__ __forceinline__ void operator()() const {}
 };
 
+// FULL mode: one distinct row's results, width wi's on lane wi, written by lanes 0..n_w-1 for
+// every DM of the row (a DM's widths are contiguous: one store per DM and array).
+__device__ __forceinline__ void full_store_row(const SearchParams &p, const int32_t *info, int64_t pix, int lane,
+                                               float fs, int ft) {
+    if (lane < p.n_w) {
+        const int fd = info[UI_FIRST_D], ndm = info[UI_N_D];
+        const int16_t t16 = static_cast<int16_t>(ft == INT_MAX ? -1 : ft);
+        for (int d = fd; d < fd + ndm; ++d) {
+            const int64_t o = (pix * p.n_dm + d) * p.n_w + lane;
+            p.full_snr[o] = fs;
+            p.full_t[o] = t16;
+        }
+    }
+}
+
 // The search of one warp over the distinct DM rows [u_lo, u_hi) of one pixel whose
 // subband rows are in xs (pitch Tp, -inf beyond the window): de-dispersion by row
 // differences, prefix sums, the boxcars of every width class, the warp arg-max and,
@@ -650,15 +665,13 @@ __device__ __forceinline__ PixRec search_rows(const SearchParams &p, const float
                 lw = wi;
             }
         };
-        // FULL mode: the S/N of (row u, width wi) reduced over the warp, and its TOA
+        // FULL mode: the S/N of (row u, width wi) reduced over the warp, and its TOA, kept on lane wi
+        float fs = neg_inf();
+        int ft = INT_MAX;
         auto write_full = [&](int wi, float s, int t) {
-            if (lane == 0) {
-                const int fd = info[UI_FIRST_D], ndm = info[UI_N_D];
-                for (int d = fd; d < fd + ndm; ++d) {
-                    const int64_t o = (pix * p.n_dm + d) * p.n_w + wi;
-                    p.full_snr[o] = s;
-                    p.full_t[o] = static_cast<int16_t>(t == INT_MAX ? -1 : t);
-                }
+            if (lane == wi) {
+                fs = s;
+                ft = t;
             }
         };
         {
@@ -745,6 +758,7 @@ if constexpr (FULL) {                                                           
                 write_full(wi, sw, t);
             }
         }
+        if constexpr (FULL) full_store_row(p, info, pix, lane, fs, ft);
 
         // warp arg-max over (S/N, width index)
 #pragma unroll
@@ -944,14 +958,13 @@ __device__ __forceinline__ PixRec search_rows_even(const SearchParams &p, const 
 
         float ls = neg_inf();
         int lw = -1;
+        // FULL mode: (row u, width wi) reduced over the warp, kept on lane wi
+        float fs = neg_inf();
+        int ft = INT_MAX;
         auto write_full = [&](int wi, float s, int t) {
-            if (lane == 0) {
-                const int fd = info[UI_FIRST_D], ndm = info[UI_N_D];
-                for (int d = fd; d < fd + ndm; ++d) {
-                    const int64_t o = (pix * p.n_dm + d) * p.n_w + wi;
-                    p.full_snr[o] = s;
-                    p.full_t[o] = static_cast<int16_t>(t == INT_MAX ? -1 : t);
-                }
+            if (lane == wi) {
+                fs = s;
+                ft = t;
             }
         };
         {
@@ -1052,6 +1065,7 @@ __device__ __forceinline__ PixRec search_rows_even(const SearchParams &p, const 
                 write_full(wi, sw, t);
             }
         }
+        if constexpr (FULL) full_store_row(p, info, pix, lane, fs, ft);
 
         // warp arg-max over (S/N, width index), only when some lane beats the warp's best
         if (__any_sync(kFull, ls > bsnr)) {
@@ -1101,6 +1115,21 @@ __device__ __forceinline__ PixRec search_rows_any(const SearchParams &p, const v
 }
 
 // ------------------------------------------------------------------ the kernel
+
+// FULL mode: -inf S/N and TOA -1 for every (DM, width) of the distinct rows [u0, u1) of a pixel
+// (rows whose delays leave no sample, or every row of a pixel without a noise scale); one warp.
+__device__ __forceinline__ void full_fill_empty(const SearchParams &p, const int32_t *s_info, int u0, int u1,
+                                                int64_t pix, int lane) {
+    for (int u = u0; u < u1; ++u) {
+        const int32_t *info = s_info + u * kInfo;
+        const int fd = info[UI_FIRST_D], ndm = info[UI_N_D];
+        for (int i = lane; i < ndm * p.n_w; i += 32) {
+            const int64_t o = (pix * p.n_dm + fd) * p.n_w + i;
+            p.full_snr[o] = neg_inf();
+            p.full_t[o] = -1;
+        }
+    }
+}
 
 template <int C, bool FULL>
 __global__ void __launch_bounds__(kThreads, 1) search_kernel(const __grid_constant__ SearchParams p) {
@@ -1304,17 +1333,7 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel(const __grid_consta
         const float bsnr = wr.snr;
         const int bu = wr.dm_idx, bwi = wr.w_idx, bt = wr.t_idx;
         // FULL mode: DM rows that have no trial at all
-        if (p.full_snr && warp == 0) {
-            for (int u = bad_pixel ? 0 : n_ua; u < p.n_u; ++u) {
-                const int32_t *info = s_info + u * kInfo;
-                const int fd = info[UI_FIRST_D], ndm = info[UI_N_D];
-                for (int i = lane; i < ndm * p.n_w; i += 32) {
-                    const int64_t o = (pix * p.n_dm + fd) * p.n_w + i;
-                    p.full_snr[o] = neg_inf();
-                    p.full_t[o] = -1;
-                }
-            }
-        }
+        if (p.full_snr && warp == 0) full_fill_empty(p, s_info, bad_pixel ? 0 : n_ua, p.n_u, pix, lane);
         if (lane == 0) s_wbest[warp] = PixRec{bsnr, bu, bwi, bt};
         __syncthreads();
         if (tid == 0) {
@@ -1338,8 +1357,8 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel(const __grid_consta
 
 // ------------------------------------------------------------------ barrier-free kernel
 
-// Same search (rows bulk-copied straight into a double buffer, KNOWN noise, per-pixel records only)
-// without CTA barriers between pixels.  The CTA's warps form TEAMS teams of W = kWarps / TEAMS warps;
+// Same search (rows bulk-copied straight into a double buffer, KNOWN noise; per-pixel records, and
+// with FULL every (DM, width) result of the pixel) without CTA barriers between pixels.  The CTA's warps form TEAMS teams of W = kWarps / TEAMS warps;
 // each team walks its own pixels (items team, team + TEAMS * grid, ... of the CTA) with its own
 // double buffer, so a pixel's distinct DM rows are split into W groups (fewer teams: more groups,
 // each built from scratch; more teams: more pixels in shared memory).  Within a team every warp
@@ -1360,7 +1379,7 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel(const __grid_consta
 // is copied from the 16-byte boundary below it and read from element eoff = t_off mod (16 / size)
 // of the staged row; when the copy then carries samples past the window, the de-dispersed samples
 // past the valid range are set to -inf instead of relying on -inf past the window.
-template <int C, int ST, int TEAMS, int NB>
+template <int C, int ST, int TEAMS, int NB, bool FULL>
 __global__ void __launch_bounds__(kThreads, 1) search_kernel_pipe(const __grid_constant__ SearchParams p) {
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr int kEs = (ST == 0) ? 4 : 2;          // bytes per stored sample
@@ -1492,11 +1511,18 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel_pipe(const __grid_c
         };
         PixRec wr;
         if constexpr (kEarly)
-            wr = search_rows_any<C, false, ST>(p, s_xs + sl * buf_bytes, Pw, Sw, s_inv + rs * kMaxW, s_info, s_delta,
-                                               s_shift, u_lo, u_hi, pix, lane, eoff, mask_tail, read_done);
+            wr = search_rows_any<C, FULL, ST>(p, s_xs + sl * buf_bytes, Pw, Sw, s_inv + rs * kMaxW, s_info, s_delta,
+                                              s_shift, u_lo, u_hi, pix, lane, eoff, mask_tail, read_done);
         else
-            wr = search_rows_any<C, false, ST>(p, s_xs + sl * buf_bytes, Pw, Sw, s_inv + rs * kMaxW, s_info, s_delta,
-                                               s_shift, u_lo, u_hi, pix, lane, eoff, mask_tail);
+            wr = search_rows_any<C, FULL, ST>(p, s_xs + sl * buf_bytes, Pw, Sw, s_inv + rs * kMaxW, s_info, s_delta,
+                                              s_shift, u_lo, u_hi, pix, lane, eoff, mask_tail);
+        // FULL mode: a pixel whose MAD is zero has no trial; its rows' entries become -inf / -1
+        if constexpr (FULL) {
+            if (p.bad_pix && p.bad_pix[pix]) {
+                __syncwarp();
+                full_fill_empty(p, s_info, u_lo, u_hi, pix, lane);
+            }
+        }
         // publish; this warp's reads of buffer sl are done before the copy that refills it
         fence_proxy_async();
         int last = 0;
@@ -1522,6 +1548,8 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel_pipe(const __grid_c
                 p.rec[pix] = best;
                 s_cnt[rs] = 0;
             }
+            // FULL mode: DM rows that have no trial at all
+            if constexpr (FULL) full_fill_empty(p, s_info, n_ua, p.n_u, pix, lane);
             __syncwarp();
             const int64_t nxt = it + NB * G;
             if (!kEarly && nxt < n_items) {
@@ -1542,11 +1570,17 @@ __global__ void __launch_bounds__(kThreads, 1) search_kernel_pipe(const __grid_c
 // and storage type (16-bit rows read in place need the sample-pair path of even chunks).
 #define NSFRB_PIPE_CASE(CC, ST, T, B)                                                          \
     case 10 * T + B:                                                                           \
-        dev::search_kernel_pipe<CC, ST, T, B><<<grid, kThreads, smem, s>>>(p);                 \
+        if (p.full_snr)                                                                        \
+            dev::search_kernel_pipe<CC, ST, T, B, true><<<grid, kThreads, smem, s>>>(p);       \
+        else                                                                                   \
+            dev::search_kernel_pipe<CC, ST, T, B, false><<<grid, kThreads, smem, s>>>(p);      \
         break;
 #define NSFRB_PIPE_ATTR1(CC, ST, T, B)                                                         \
     if (e == cudaSuccess)                                                                      \
-        e = cudaFuncSetAttribute(dev::search_kernel_pipe<CC, ST, T, B>,                        \
+        e = cudaFuncSetAttribute(dev::search_kernel_pipe<CC, ST, T, B, false>,                 \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, sm);             \
+    if (e == cudaSuccess)                                                                      \
+        e = cudaFuncSetAttribute(dev::search_kernel_pipe<CC, ST, T, B, true>,                  \
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
 #define NSFRB_INSTANTIATE_PIPE(CC, ST)                                                         \
     cudaError_t launch_pipe_c##CC##_s##ST(const SearchParams &p, int grid, size_t smem, cudaStream_t s) { \

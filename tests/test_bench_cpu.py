@@ -32,12 +32,14 @@ def test_reference_arm_prints_one_json_line():
 def test_search_kernel_name_follows_the_chunk_rule():
     sys.path.insert(0, ROOT)
     import bench
-    assert bench.search_kernel_name(1200, "f32") == "search_kernel_pipe<38, 0>"
-    assert bench.search_kernel_name(1200, "bf16") == "search_kernel_pipe<38, 1>"
+    assert bench.search_kernel_name(1200, "f32") == "search_kernel_pipe<38, 0, T, B, 0>"
+    assert bench.search_kernel_name(1200, "bf16") == "search_kernel_pipe<38, 1, T, B, 0>"
     assert bench.search_kernel_name(1200, "bf16", "mad", 21) == \
-        "mad_normalise_kernel + search_kernel_pipe<38, 0, 2, 1> (FP32 slabs)"
-    assert bench.search_kernel_name(1200, "bf16", tile=41) == "search_kernel_pipe<38, 1, 4, 1>"
-    assert bench.search_kernel_name(1247, "f32") == "search_kernel_pipe<39, 0>"
-    assert bench.search_kernel_name(4096, "bf16") == "search_kernel_long<1, false>"
-    assert bench.search_kernel_name(64, "f32") == "search_kernel_pipe<3, 0>"
-    assert bench.search_kernel_name(1001, "bf16") == "search_kernel<38, false>"
+        "mad_normalise_kernel + search_kernel_pipe<38, 0, 2, 1, 0> (FP32 slabs)"
+    assert bench.search_kernel_name(1200, "bf16", tile=41) == "search_kernel_pipe<38, 1, 4, 1, 0>"
+    assert bench.search_kernel_name(1200, "f32", tile=21, out="full") == "search_kernel_pipe<38, 0, 2, 1, 1>"
+    assert bench.search_kernel_name(1247, "f32") == "search_kernel_pipe<39, 0, T, B, 0>"
+    assert bench.search_kernel_name(4096, "bf16") == "search_kernel_long<1, 0>"
+    assert bench.search_kernel_name(4096, "f32", out="full") == "search_kernel_long<0, 1>"
+    assert bench.search_kernel_name(64, "f32") == "search_kernel_pipe<3, 0, T, B, 0>"
+    assert bench.search_kernel_name(1001, "bf16") == "search_kernel<38, 0>"

@@ -201,6 +201,31 @@ def test_mad_zero_is_reported(native):
     assert snr[2] == -np.inf and np.isfinite(snr[[0, 1, 3]]).all()
 
 
+@pytest.mark.parametrize("n_t", [48, 50])
+def test_mad_zero_full_arrays(native, n_t):
+    """FULL arrays with a zero-MAD pixel: that pixel has no trial at any (DM, width) (-inf, -1);
+    every other pixel's entries equal the oracle's (windows of whole 16-byte units take the
+    barrier-free kernel on the normalised slabs, others the staged kernel)."""
+    cfg = synth.SearchConfig(ny=2, nx=3, n_t=n_t, dm=np.array([0.0, 100.0, 400.0, 30000.0]),
+                             widths=np.array([1, 3, 8], np.int32))
+    rng = np.random.default_rng(n_t)
+    cube = torch.from_numpy(rng.standard_normal((cfg.n_pix, cfg.n_sub, n_t)).astype(np.float32))
+    cube[2, 5] = 1.0    # constant row: MAD = 0
+    plan = native.Plan(cfg, noise="mad", out="full")
+    plan.search(cube.cuda())
+    with pytest.raises(native.NsfrbError):
+        plan.candidates()
+    f_snr, f_t = plan.full()
+    plan.close()
+    assert np.all(f_snr[2] == -np.inf) and np.all(f_t[2] == -1)
+    keep = np.array([0, 1, 3, 4, 5])
+    tab, res, best, bad = _oracle(cfg, cube.numpy(), mad=True, pix=keep)
+    assert bad == 0
+    xs = oracle.mad_normalise(cube.numpy()[keep])[0]
+    parity.compare_full(f_snr[keep], f_t[keep], res, x=xs, sigma=math.sqrt(cfg.n_sub), shifts=tab,
+                        widths=cfg.widths)
+
+
 # ----------------------------------------------------------------------------- host entry point
 
 def test_search_host_matches_device(native):
@@ -358,3 +383,29 @@ def test_every_tile_matches_oracle(native, dtype, noise, n_t):
         checked.append(tile)
     plan.close()
     assert sorted(checked) == sorted(ms)
+
+
+@pytest.mark.parametrize("dtype,n_t", [("f32", 1200), ("bf16", 1200), ("f32", 100)])
+def test_every_tile_full_arrays(native, dtype, n_t):
+    """FULL arrays from every (teams, buffers) tile of the barrier-free kernel equal the oracle's."""
+    rng = np.random.default_rng(n_t + 3 * len(dtype))
+    tdt = {"f32": torch.float32, "bf16": torch.bfloat16}[dtype]
+    widths = [w for w in [1, 2, 3, 4, 8, 16, 32, 64, 100, 128, 256, 512, 1024] if w <= n_t]
+    cfg = synth.SearchConfig(ny=5, nx=7, n_t=n_t, dm=np.sort(rng.uniform(0, 2500, 29)),
+                             widths=np.array(widths, np.int32), threshold=4.5)
+    cube = _psf_cube(cfg, n_t, 4, dm_range=(0.0, 2500.0)).to(tdt)
+    sig = rng.uniform(4.0, 8.0, cfg.n_pix).astype(np.float32)
+    dev, sg = cube.cuda(), torch.as_tensor(sig).cuda()
+    x = cube.float().numpy()
+    tab, res, best, bad = _oracle(cfg, x, sigma=sig)
+    plan = native.Plan(cfg, dtype=dtype, out="full")
+    _, ms = plan.autotune(dev, sg, reps=1)
+    assert 12 in ms and len(ms) >= 2
+    for tile in ms:
+        plan.set_tile(plan.dtype, tile)
+        plan.search(dev, sg)
+        f_snr, f_t = plan.full()
+        parity.compare_full(f_snr, f_t, res, x=x, sigma=sig, shifts=tab, widths=cfg.widths)
+        snr, idx = plan.best()
+        parity.compare_best(snr, idx, best)
+    plan.close()
