@@ -154,15 +154,15 @@ __device__ __forceinline__ float fmax3(float a, float b, float c) {
     return d;
 }
 
-// max over f(0..N-1) with four independent accumulators of 3-input maxima, so
-// that the reduction is four short dependency chains instead of one long one.
+// max over f(0..N-1) with three independent accumulators of 3-input maxima (three short
+// dependency chains instead of one long one), combined by one more 3-input maximum.
 template <int N, typename F>
 __device__ __forceinline__ float tree_max(F f) {
-    float acc[4] = {neg_inf(), neg_inf(), neg_inf(), neg_inf()};
+    float acc[3] = {neg_inf(), neg_inf(), neg_inf()};
 #pragma unroll
-    for (int j = 0; j + 1 < N; j += 2) acc[(j >> 1) & 3] = fmax3(acc[(j >> 1) & 3], f(j), f(j + 1));
-    if constexpr (N & 1) acc[3] = fmaxf(acc[3], f(N - 1));
-    return fmaxf(fmaxf(acc[0], acc[1]), fmaxf(acc[2], acc[3]));
+    for (int j = 0; j + 1 < N; j += 2) acc[(j >> 1) % 3] = fmax3(acc[(j >> 1) % 3], f(j), f(j + 1));
+    if constexpr (N & 1) acc[2] = fmaxf(acc[2], f(N - 1));
+    return fmax3(acc[0], acc[1], acc[2]);
 }
 
 // In-lane small width W: B[c] = P[t0+c+W] - P[t0+c] from the in-lane prefix Lp
@@ -442,7 +442,34 @@ __device__ __forceinline__ void dd_first(float2 (&D)[C / 2], const void *xs, int
     for (int k = 0; k < n_sub; ++k) acc_row<C, false, ST>(D, xs, Tp, k, t0 + sh[k]);
 }
 
-// Next row from the previous one: per changed subband, D = (D + x_k(t + s_new)) - x_k(t + s_old).
+// D[c] += x[c + 1] - x[c] for c < C, xr = subband row + t0 + s (FP32): a subband whose shift grew
+// by one sample, both terms from one read of the row.  The two differences of a pair are scalar
+// (they straddle the loaded pairs), their sum with D a two-lane add.
+template <int C>
+__device__ __forceinline__ void acc_step1(float2 (&D)[C / 2], const float *xr, bool odd) {
+    if (!odd) {
+        const float2 *x = reinterpret_cast<const float2 *>(xr);     // x[m] = (xr[2m], xr[2m + 1])
+        float2 v = x[0];
+#pragma unroll
+        for (int m = 0; m < C / 2; ++m) {
+            const float2 nx = x[m + 1];
+            D[m] = add2(D[m], make_float2(v.y - v.x, nx.x - v.y));
+            v = nx;
+        }
+    } else {
+        const float2 *x = reinterpret_cast<const float2 *>(xr - 1); // x[m] = (xr[2m - 1], xr[2m])
+        float a = x[0].y;
+#pragma unroll
+        for (int m = 0; m < C / 2; ++m) {
+            const float2 nx = x[m + 1];
+            D[m] = add2(D[m], make_float2(nx.x - a, nx.y - nx.x));
+            a = nx.y;
+        }
+    }
+}
+
+// Next row from the previous one: per changed subband, D = (D + x_k(t + s_new)) - x_k(t + s_old),
+// or for FP32 rows whose shift grew by one sample D = D + (x_k(t + s_old + 1) - x_k(t + s_old)).
 template <int C, int ST>
 __device__ __forceinline__ void dd_delta(float2 (&D)[C / 2], const void *xs, int Tp, const int32_t *s_delta,
                                          int d0, int nd, int t0) {
@@ -450,6 +477,13 @@ __device__ __forceinline__ void dd_delta(float2 (&D)[C / 2], const void *xs, int
     for (int e = d0; e < d0 + nd; ++e) {
         const uint32_t pk = static_cast<uint32_t>(s_delta[e]);
         const int k = pk & 63u, so = (pk >> 6) & 0x1fffu, sn = pk >> 19;
+        if constexpr (ST == 0) {
+            if (sn == so + 1) {
+                const int at = t0 + so;
+                acc_step1<C>(D, static_cast<const float *>(xs) + (size_t)k * Tp + at, at & 1);
+                continue;
+            }
+        }
         acc_row<C, false, ST>(D, xs, Tp, k, t0 + sn);
         acc_row<C, true, ST>(D, xs, Tp, k, t0 + so);
     }
@@ -471,16 +505,18 @@ __device__ __forceinline__ float prefix_pairs(const float2 (&D)[C / 2], float2 (
             tot = run;
     }
     if constexpr (C > H1) {
-        float q = 0.0f;
+        // second chain q[j] = D[H1] + ... + D[H1 + j], then Lp[H1 + 1 + j] = run + q[j]; H1 + 1 is
+        // odd (C even), so the offsets of the whole pairs (Lp[H1 + 2], Lp[H1 + 3]) ... (Lp[C - 2],
+        // Lp[C - 1]) are two-lane adds (each lane rounds like the scalar add: the same values)
+        float q[C - H1];
+        q[0] = pget(D, H1);
 #pragma unroll
-        for (int j = 0; j < C - H1; ++j) {
-            q = (j == 0) ? pget(D, H1) : q + pget(D, H1 + j);
-            const float v = run + q;
-            if (H1 + 1 + j < C)
-                pset(Lp, H1 + 1 + j, v);
-            else
-                tot = v;
-        }
+        for (int j = 1; j < C - H1; ++j) q[j] = q[j - 1] + pget(D, H1 + j);
+        if constexpr (H1 + 1 < C) pset(Lp, H1 + 1, run + q[0]);
+        const float2 rr = make_float2(run, run);
+#pragma unroll
+        for (int i = H1 + 2; i + 1 < C; i += 2) Lp[i >> 1] = add2(rr, make_float2(q[i - H1 - 1], q[i - H1]));
+        tot = run + q[C - H1 - 1];
     }
     return tot;
 }
@@ -495,16 +531,17 @@ __device__ __forceinline__ void store_p(float *Pw, int t0, float carry, const fl
 }
 
 // Halo as pairs: Hh holds h[i] for i < SH, h[0] = the lane total (= Lp[C]) and
-// h[i] = total + the next lane's Lp[i] (NaN on the last lane), so that the extended in-lane
-// prefix E = (Lp[0..C), h[0..SH)) pairs up as (E[2j], E[2j+1]).
+// h[i] = total + the next lane's Lp[i], so that the extended in-lane prefix
+// E = (Lp[0..C), h[0..SH)) pairs up as (E[2j], E[2j+1]).  The last lane needs no mask: its chunk
+// ends at sample 32 C - 1 >= n_t, whose de-dispersed value is -inf or NaN (-inf past the window,
+// NaN where a row difference subtracted -inf from -inf), so its total and every h[i] are -inf or
+// NaN, and each trial that reads them drops out of every maximum and never equals a target.
+// (Only the unmasked search calls this; a masked search evaluates no in-lane widths.)
 template <int C, int SH>
-__device__ __forceinline__ void halo_pairs(const float2 (&Lp)[C / 2], float tot, int lane, float2 (&Hh)[SH / 2]) {
+__device__ __forceinline__ void halo_pairs(const float2 (&Lp)[C / 2], float tot, float2 (&Hh)[SH / 2]) {
     Hh[0].x = tot;
 #pragma unroll
-    for (int i = 1; i < SH; ++i) {
-        const float v = __shfl_down_sync(kFull, pget(Lp, i), 1);
-        pset(Hh, i, (lane == 31) ? qnan() : tot + v);
-    }
+    for (int i = 1; i < SH; ++i) pset(Hh, i, tot + __shfl_down_sync(kFull, pget(Lp, i), 1));
 }
 
 template <int C, int SH>
@@ -522,7 +559,7 @@ template <int C, int SH, int W>
 __device__ __forceinline__ float small_max_pk(const float2 (&D)[C / 2], const float2 (&Lp)[C / 2],
                                               const float2 (&Hh)[SH / 2]) {
     static_assert(W == 1 || W % 2 == 0, "in-lane widths are 1 or even");
-    float acc[4] = {neg_inf(), neg_inf(), neg_inf(), neg_inf()};
+    float acc[3] = {neg_inf(), neg_inf(), neg_inf()};
 #pragma unroll
     for (int m = 0; m < C / 2; ++m) {
         float2 b;
@@ -530,9 +567,9 @@ __device__ __forceinline__ float small_max_pk(const float2 (&D)[C / 2], const fl
             b = D[m];
         else
             b = sub2(ext_pair<C, SH>(Lp, Hh, m + W / 2), ext_pair<C, SH>(Lp, Hh, m));
-        acc[m & 3] = fmax3(acc[m & 3], b.x, b.y);
+        acc[m % 3] = fmax3(acc[m % 3], b.x, b.y);
     }
-    return fmaxf(fmaxf(acc[0], acc[1]), fmaxf(acc[2], acc[3]));
+    return fmax3(acc[0], acc[1], acc[2]);
 }
 
 template <int C, int SH, int W>
@@ -572,13 +609,13 @@ __device__ __forceinline__ void load_ps(const float *Pw, int lane, float2 (&Ps)[
 template <int C, int M>
 __device__ __forceinline__ float large_max_pk(const float2 (&Ps)[C / 2]) {
     if constexpr (M % 2 == 0) {
-        float acc[4] = {neg_inf(), neg_inf(), neg_inf(), neg_inf()};
+        float acc[3] = {neg_inf(), neg_inf(), neg_inf()};
 #pragma unroll
         for (int m = 0; m < (C - M) / 2; ++m) {
             const float2 b = sub2(Ps[m + M / 2], Ps[m]);
-            acc[m & 3] = fmax3(acc[m & 3], b.x, b.y);
+            acc[m % 3] = fmax3(acc[m % 3], b.x, b.y);
         }
-        return fmaxf(fmaxf(acc[0], acc[1]), fmaxf(acc[2], acc[3]));
+        return fmax3(acc[0], acc[1], acc[2]);
     } else {
         return tree_max<C - M>([&](int i) { return pget(Ps, i + M) - pget(Ps, i); });
     }
@@ -913,7 +950,7 @@ __device__ __forceinline__ int find_t_even(const SearchParams &p, const float2 (
         float2 Lp[C / 2];
         float2 Hh[SH / 2];
         const float tot = prefix_pairs<C>(D, Lp);
-        halo_pairs<C, SH>(Lp, tot, lane, Hh);
+        halo_pairs<C, SH>(Lp, tot, Hh);
         return small_find_coop_w<C, SH>(w, D, Lp, Hh, scr, match, lane, inv, target);
     }
     return large_find_coop<C>(Pw, w >> 5, match, lane, inv, target);
@@ -970,12 +1007,14 @@ __device__ __forceinline__ PixRec search_rows_even(const SearchParams &p, const 
         {
             float2 Lp[C / 2];
             const float tot = prefix_pairs<C>(D, Lp);
-            store_p<C>(Pw, t0, lane_carry(tot, lane), Lp);
             if (!masked && p.has_small) {
                 // power-of-two widths <= min(C, 16) in-lane; ascending width order with a
-                // strict '>' keeps the smallest width index on ties
+                // strict '>' keeps the smallest width index on ties.  The warp scan of the lane
+                // totals and the store of P sit in the same block, so that the scan's shuffle
+                // chain overlaps the in-lane widths, which do not need it.
                 float2 Hh[SH / 2];
-                halo_pairs<C, SH>(Lp, tot, lane, Hh);
+                halo_pairs<C, SH>(Lp, tot, Hh);
+                const float carry = lane_carry(tot, lane);
 #define NSFRB_SMALL_PK(J)                                                                                 \
     if constexpr (pow2_class(C, J) == WC_SMALL) {                                                        \
         const int wi = p.pow2_wi[J];                                                                      \
@@ -998,6 +1037,9 @@ __device__ __forceinline__ PixRec search_rows_even(const SearchParams &p, const 
     }
                 NSFRB_SMALL_PK(0) NSFRB_SMALL_PK(1) NSFRB_SMALL_PK(2) NSFRB_SMALL_PK(3) NSFRB_SMALL_PK(4)
 #undef NSFRB_SMALL_PK
+                store_p<C>(Pw, t0, carry, Lp);
+            } else {
+                store_p<C>(Pw, t0, lane_carry(tot, lane), Lp);
             }
         }
         __syncwarp();
