@@ -468,8 +468,55 @@ __device__ __forceinline__ void acc_step1(float2 (&D)[C / 2], const float *xr, b
     }
 }
 
+// The low and high 16-bit value of a 32-bit word of a BF16 (ST = 1) or FP16 (ST = 2) row, widened
+// to FP32 (exactly).
+template <int ST>
+__device__ __forceinline__ float lo16(uint32_t u) {
+    if constexpr (ST == 1)
+        return __uint_as_float(u << 16);
+    else
+        return __half2float(__ushort_as_half(static_cast<unsigned short>(u & 0xffffu)));
+}
+template <int ST>
+__device__ __forceinline__ float hi16(uint32_t u) {
+    if constexpr (ST == 1)
+        return __uint_as_float(u & 0xffff0000u);
+    else
+        return __half2float(__ushort_as_half(static_cast<unsigned short>(u >> 16)));
+}
+
+// acc_step1 for a 16-bit row read in place as 32-bit words: D[c] += x[e + c + 1] - x[e + c], the
+// differences of the widened values in FP32.
+template <int C, int ST>
+__device__ __forceinline__ void acc_step1_16(float2 (&D)[C / 2], const uint16_t *row, int e) {
+    const uint32_t *w = reinterpret_cast<const uint32_t *>(row + (e & ~1));
+    if (!(e & 1)) {   // w[m] = (x[e + 2m], x[e + 2m + 1])
+        float a = lo16<ST>(w[0]);
+        uint32_t u = w[0];
+#pragma unroll
+        for (int m = 0; m < C / 2; ++m) {
+            const uint32_t nu = w[m + 1];
+            const float b = hi16<ST>(u), c = lo16<ST>(nu);
+            D[m] = add2(D[m], make_float2(b - a, c - b));
+            a = c;
+            u = nu;
+        }
+    } else {          // w[m] = (x[e + 2m - 1], x[e + 2m])
+        float a = hi16<ST>(w[0]);
+#pragma unroll
+        for (int m = 0; m < C / 2; ++m) {
+            const uint32_t nu = w[m + 1];
+            const float b = lo16<ST>(nu), c = hi16<ST>(nu);
+            D[m] = add2(D[m], make_float2(b - a, c - b));
+            a = c;
+        }
+    }
+}
+
 // Next row from the previous one: per changed subband, D = (D + x_k(t + s_new)) - x_k(t + s_old),
-// or for FP32 rows whose shift grew by one sample D = D + (x_k(t + s_old + 1) - x_k(t + s_old)).
+// or where the shift grew by one sample D = D + (x_k(t + s_old + 1) - x_k(t + s_old)).  (Within a
+// row the -inf past the window is a suffix, so x(t) = -inf implies x(t + 1) = -inf: the difference
+// is never +inf, and a de-dispersed value past the valid range stays -inf or NaN.)
 template <int C, int ST>
 __device__ __forceinline__ void dd_delta(float2 (&D)[C / 2], const void *xs, int Tp, const int32_t *s_delta,
                                          int d0, int nd, int t0) {
@@ -477,12 +524,13 @@ __device__ __forceinline__ void dd_delta(float2 (&D)[C / 2], const void *xs, int
     for (int e = d0; e < d0 + nd; ++e) {
         const uint32_t pk = static_cast<uint32_t>(s_delta[e]);
         const int k = pk & 63u, so = (pk >> 6) & 0x1fffu, sn = pk >> 19;
-        if constexpr (ST == 0) {
-            if (sn == so + 1) {
-                const int at = t0 + so;
+        if (sn == so + 1) {
+            const int at = t0 + so;
+            if constexpr (ST == 0)
                 acc_step1<C>(D, static_cast<const float *>(xs) + (size_t)k * Tp + at, at & 1);
-                continue;
-            }
+            else
+                acc_step1_16<C, ST>(D, static_cast<const uint16_t *>(xs) + (size_t)k * Tp, at);
+            continue;
         }
         acc_row<C, false, ST>(D, xs, Tp, k, t0 + sn);
         acc_row<C, true, ST>(D, xs, Tp, k, t0 + so);
