@@ -468,55 +468,66 @@ __device__ __forceinline__ void acc_step1(float2 (&D)[C / 2], const float *xr, b
     }
 }
 
-// The low and high 16-bit value of a 32-bit word of a BF16 (ST = 1) or FP16 (ST = 2) row, widened
-// to FP32 (exactly).
-template <int ST>
-__device__ __forceinline__ float lo16(uint32_t u) {
-    if constexpr (ST == 1)
-        return __uint_as_float(u << 16);
-    else
-        return __half2float(__ushort_as_half(static_cast<unsigned short>(u & 0xffffu)));
-}
-template <int ST>
-__device__ __forceinline__ float hi16(uint32_t u) {
-    if constexpr (ST == 1)
-        return __uint_as_float(u & 0xffff0000u);
-    else
-        return __half2float(__ushort_as_half(static_cast<unsigned short>(u >> 16)));
+// acc_step1 for a 16-bit row read in place as 32-bit words: D[c] = (D[c] + x[e + c + 1]) - x[e + c]
+// by the mixed-precision add and fma (the operations of acc_pairs16's add and subtract, from one
+// read of the row).  u, nu: the words holding the pair's samples; OD: e odd.
+template <int ST, bool OD>
+__device__ __forceinline__ void step1_pair16(float2 &d, uint32_t u, uint32_t nu) {
+    // even e: (x[2m], x[2m+1]) = (lo u, hi u), x[2m+2] = lo nu
+    //   d.x = (d.x + hi u) - lo u,  d.y = (d.y + lo nu) - hi u
+    // odd e:  x[2m] = hi u, (x[2m+1], x[2m+2]) = (lo nu, hi nu)
+    //   d.x = (d.x + lo nu) - hi u, d.y = (d.y + hi nu) - lo nu
+    if constexpr (ST == 1) {
+        if constexpr (!OD)
+            asm("{\n\t.reg .b16 ul, uh, nl, nh, m;\n\tmov.b32 {ul, uh}, %2;\n\tmov.b32 {nl, nh}, %3;\n\t"
+                "mov.b16 m, 0xBF80;\n\tadd.rn.f32.bf16 %0, uh, %0;\n\tfma.rn.f32.bf16 %0, ul, m, %0;\n\t"
+                "add.rn.f32.bf16 %1, nl, %1;\n\tfma.rn.f32.bf16 %1, uh, m, %1;\n\t}"
+                : "+f"(d.x), "+f"(d.y) : "r"(u), "r"(nu));
+        else
+            asm("{\n\t.reg .b16 ul, uh, nl, nh, m;\n\tmov.b32 {ul, uh}, %2;\n\tmov.b32 {nl, nh}, %3;\n\t"
+                "mov.b16 m, 0xBF80;\n\tadd.rn.f32.bf16 %0, nl, %0;\n\tfma.rn.f32.bf16 %0, uh, m, %0;\n\t"
+                "add.rn.f32.bf16 %1, nh, %1;\n\tfma.rn.f32.bf16 %1, nl, m, %1;\n\t}"
+                : "+f"(d.x), "+f"(d.y) : "r"(u), "r"(nu));
+    } else {
+        if constexpr (!OD)
+            asm("{\n\t.reg .b16 ul, uh, nl, nh, m;\n\tmov.b32 {ul, uh}, %2;\n\tmov.b32 {nl, nh}, %3;\n\t"
+                "mov.b16 m, 0xBC00;\n\tadd.rn.f32.f16 %0, uh, %0;\n\tfma.rn.f32.f16 %0, ul, m, %0;\n\t"
+                "add.rn.f32.f16 %1, nl, %1;\n\tfma.rn.f32.f16 %1, uh, m, %1;\n\t}"
+                : "+f"(d.x), "+f"(d.y) : "r"(u), "r"(nu));
+        else
+            asm("{\n\t.reg .b16 ul, uh, nl, nh, m;\n\tmov.b32 {ul, uh}, %2;\n\tmov.b32 {nl, nh}, %3;\n\t"
+                "mov.b16 m, 0xBC00;\n\tadd.rn.f32.f16 %0, nl, %0;\n\tfma.rn.f32.f16 %0, uh, m, %0;\n\t"
+                "add.rn.f32.f16 %1, nh, %1;\n\tfma.rn.f32.f16 %1, nl, m, %1;\n\t}"
+                : "+f"(d.x), "+f"(d.y) : "r"(u), "r"(nu));
+    }
 }
 
-// acc_step1 for a 16-bit row read in place as 32-bit words: D[c] += x[e + c + 1] - x[e + c], the
-// differences of the widened values in FP32.
 template <int C, int ST>
 __device__ __forceinline__ void acc_step1_16(float2 (&D)[C / 2], const uint16_t *row, int e) {
     const uint32_t *w = reinterpret_cast<const uint32_t *>(row + (e & ~1));
-    if (!(e & 1)) {   // w[m] = (x[e + 2m], x[e + 2m + 1])
-        float a = lo16<ST>(w[0]);
-        uint32_t u = w[0];
+    uint32_t u = w[0];
+    if (!(e & 1)) {
 #pragma unroll
         for (int m = 0; m < C / 2; ++m) {
             const uint32_t nu = w[m + 1];
-            const float b = hi16<ST>(u), c = lo16<ST>(nu);
-            D[m] = add2(D[m], make_float2(b - a, c - b));
-            a = c;
+            step1_pair16<ST, false>(D[m], u, nu);
             u = nu;
         }
-    } else {          // w[m] = (x[e + 2m - 1], x[e + 2m])
-        float a = hi16<ST>(w[0]);
+    } else {
 #pragma unroll
         for (int m = 0; m < C / 2; ++m) {
             const uint32_t nu = w[m + 1];
-            const float b = lo16<ST>(nu), c = hi16<ST>(nu);
-            D[m] = add2(D[m], make_float2(b - a, c - b));
-            a = c;
+            step1_pair16<ST, true>(D[m], u, nu);
+            u = nu;
         }
     }
 }
 
 // Next row from the previous one: per changed subband, D = (D + x_k(t + s_new)) - x_k(t + s_old),
-// or where the shift grew by one sample D = D + (x_k(t + s_old + 1) - x_k(t + s_old)).  (Within a
-// row the -inf past the window is a suffix, so x(t) = -inf implies x(t + 1) = -inf: the difference
-// is never +inf, and a de-dispersed value past the valid range stays -inf or NaN.)
+// both from one read of the row where the shift grew by one sample; for FP32 rows that case is
+// D = D + (x_k(t + s_old + 1) - x_k(t + s_old)).  (Within a row the -inf past the window is a
+// suffix, so x(t) = -inf implies x(t + 1) = -inf: the difference is never +inf, and a de-dispersed
+// value past the valid range stays -inf or NaN.)
 template <int C, int ST>
 __device__ __forceinline__ void dd_delta(float2 (&D)[C / 2], const void *xs, int Tp, const int32_t *s_delta,
                                          int d0, int nd, int t0) {
