@@ -607,10 +607,6 @@ template <int C, int SH>
 __device__ __forceinline__ float2 ext_pair(const float2 (&Lp)[C / 2], const float2 (&Hh)[SH / 2], int j) {
     return (j < C / 2) ? Lp[j] : Hh[j - C / 2];
 }
-template <int C, int SH>
-__device__ __forceinline__ float ext_at(const float2 (&Lp)[C / 2], const float2 (&Hh)[SH / 2], int i) {
-    return (i < C) ? pget(Lp, i) : pget(Hh, i - C);
-}
 
 // In-lane width W <= SH: W = 1 is the de-dispersed sample itself; an even W is the difference
 // of extended prefix pairs W / 2 apart.
@@ -629,32 +625,6 @@ __device__ __forceinline__ float small_max_pk(const float2 (&D)[C / 2], const fl
         acc[m % 3] = fmax3(acc[m % 3], b.x, b.y);
     }
     return fmax3(acc[0], acc[1], acc[2]);
-}
-
-template <int C, int SH, int W>
-__device__ __forceinline__ int small_find_pk_w(const float2 (&D)[C / 2], const float2 (&Lp)[C / 2],
-                                               const float2 (&Hh)[SH / 2], float inv, float target, int t0) {
-    int found = INT_MAX;
-#pragma unroll
-    for (int c = C - 1; c >= 0; --c) {
-        const float b = (W == 1) ? pget(D, c) : ext_at<C, SH>(Lp, Hh, c + W) - ext_at<C, SH>(Lp, Hh, c);
-        if (b * inv == target) found = t0 + c;
-    }
-    return found;
-}
-
-template <int C, int SH>
-__device__ __forceinline__ int small_find_pk(int w, const float2 (&D)[C / 2], const float2 (&Lp)[C / 2],
-                                             const float2 (&Hh)[SH / 2], float inv, float target, int t0) {
-    switch (w) {
-        case 1: return small_find_pk_w<C, SH, 1>(D, Lp, Hh, inv, target, t0);
-        case 2: if constexpr (2 <= SH) return small_find_pk_w<C, SH, 2>(D, Lp, Hh, inv, target, t0); break;
-        case 4: if constexpr (4 <= SH) return small_find_pk_w<C, SH, 4>(D, Lp, Hh, inv, target, t0); break;
-        case 8: if constexpr (8 <= SH) return small_find_pk_w<C, SH, 8>(D, Lp, Hh, inv, target, t0); break;
-        case 16: if constexpr (16 <= SH) return small_find_pk_w<C, SH, 16>(D, Lp, Hh, inv, target, t0); break;
-        default: break;
-    }
-    return INT_MAX;
 }
 
 // Lane-strided P as pairs: Ps[m] = (P[64 m + lane], P[64 m + 32 + lane]).
