@@ -75,6 +75,8 @@ def parse():
                     help="timed launches of the imager section, one 25-sample block each (0: skip)")
     ap.add_argument("--stress-steps", type=int, default=5,
                     help="timed searches of the 512x512 BF16 MAD stress workload (0: skip)")
+    ap.add_argument("--timescale-steps", type=int, default=5,
+                    help="timed 0.67 s and 10.05 s searches of the bench cube and PSF clusterings (0: skip)")
     ap.add_argument("--stress-size", type=int, default=512,
                     help="side of the stress image (512 is the stress workload; smaller for profiling)")
     ap.add_argument("--serving-fields", default="301x301,257x257,193x193,129x129",
@@ -686,6 +688,59 @@ def imager_section(native, steps: int, seed: int = 0):
                              "sample": f"{len(pairs)} images of the block, FP64 numpy"}}
 
 
+def timescales_section(native, synth, cube, cfg, sigma, cand, steps: int):
+    """The 0.67 s and 10.05 s searches of the bench cube (Sec. 2.2 and its footnote): per scale the
+    time binning (nsfrb_bin_time, HBM-bound: the cube read once, 1/factor of it written) and the
+    search of the binned cube (widths 1..16, DM x5 on the same integer shifts, or DM 0), both timed
+    with CUDA events on the launching stream; and the PSF clustering of the full-resolution
+    candidate list (Sec. 2.3, nsfrb_psf_cluster), timed per call with its copies."""
+    import torch
+    from paper_2510_18136_gb300 import multiscale
+    pk = peaks()
+    stream = torch.cuda.current_stream()
+    in_bytes = cube.numel() * cube.element_size()
+    out = {"cube": f"{cfg.ny}x{cfg.nx} px x {cfg.n_sub} sub x {cfg.n_t} samples ({cube.dtype})", "scales": []}
+    for factor, c in multiscale.paper_timescales(cfg)[1:]:
+        sg = sigma * math.sqrt(factor)
+        plan = native.Plan(c, dtype="f32")
+        for _ in range(2):   # warm-up (allocates the binned cube, loads the kernels)
+            xb = multiscale.bin_time(cube, factor, stream=stream)
+            plan.search(xb, sg, stream=stream)
+            plan.candidates()
+        bin_ms, search_ms, n_c = [], [], 0
+        for _ in range(steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            xb = multiscale.bin_time(cube, factor, stream=stream)
+            e1.record(stream)
+            plan.search(xb, sg, stream=stream)
+            n_c = len(plan.candidates())
+            bin_ms.append(e0.elapsed_time(e1))
+            search_ms.append(plan.last_timing()[0])
+        plan.close()
+        b_ms, k_ms = statistics.median(bin_ms), statistics.median(search_ms)
+        bin_bytes = in_bytes + xb.numel() * 4
+        out["scales"].append({
+            "factor": factor, "t_samp_ms": c.t_samp_ms, "n_t": c.n_t, "n_dm": len(c.dm),
+            "widths": [int(w) for w in c.widths], "bin_ms": b_ms, "search_ms": k_ms,
+            "trials_per_s": c.n_trials / ((b_ms + k_ms) / 1e3), "candidates": n_c,
+            "bin_roofline": {"bound": "hbm", "achieved": bin_bytes / (b_ms / 1e3) / 1e9, "peak": pk["hbm_gbs"],
+                             "unit": "GB/s", "frac": bin_bytes / (b_ms / 1e3) / 1e9 / pk["hbm_gbs"],
+                             "bytes_per_launch": bin_bytes}})
+    psf = synth.gaussian_psf(15).astype(np.float32)
+    native.psf_cluster(cand, cfg.nx, psf)
+    t = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        top, res = native.psf_cluster(cand, cfg.nx, psf)
+        t.append(time.perf_counter() - t0)
+    out["psf_cluster"] = {"candidates_in": int(len(cand)), "top_k": 10, "psf": "15x15 Gaussian",
+                          "ms_per_call": statistics.median(t) * 1e3, "n_top": int(res["n_top"]),
+                          "timing": "host wall clock per call: candidate list to the device, kernel, result back"}
+    return out
+
+
 def stress_section(native, synth, steps: int, seed: int = 0, size: int = 512):
     """The stress workload: 512x512 px x 16 sub x 1200 samples stored in BF16, beam-scaled
     Student-t noise, MAD normalisation per (pixel, subband), 500 injections, 256 DM 0-4000,
@@ -888,6 +943,9 @@ def main():
     imager = None
     if args.imager_steps > 0 and rank == 0:
         imager = imager_section(native, args.imager_steps, seed=args.seed)
+    timescales = None
+    if args.timescale_steps > 0 and rank == 0 and args.out == "candidates":
+        timescales = timescales_section(native, synth, cube, cfg, sigma, cand, args.timescale_steps)
     stress = None
     if args.stress_steps > 0 and rank == 0:
         stress = stress_section(native, synth, args.stress_steps, seed=args.seed, size=args.stress_size)
@@ -931,6 +989,7 @@ def main():
         "campaigns": campaigns,
         "imager": imager,
         "stress": stress,
+        "timescales": timescales,
         "clocks": ck,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
