@@ -43,3 +43,37 @@ def test_search_kernel_name_follows_the_chunk_rule():
     assert bench.search_kernel_name(4096, "f32", out="full") == "search_kernel_long<0, 1>"
     assert bench.search_kernel_name(64, "f32") == "search_kernel_pipe<3, 0, T, B, 0>"
     assert bench.search_kernel_name(1001, "bf16") == "search_kernel<38, 0>"
+
+
+def test_alg_ops_counts_the_definition():
+    """The roofline's numerator (bench.alg_ops) against an explicit count of the definition's FP32
+    operations on a tiny grid: per pixel and distinct shift row u with L = n_t - max shift, each
+    valid de-dispersed sample costs n_sub - 1 adds and one prefix add, each boxcar trial of each
+    width a difference and a running maximum; rows without samples cost nothing.  Identical DMs
+    are one row; the distinct rows come from the oracle's delay table."""
+    import numpy as np
+
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle
+    from paper_2510_18136_gb300 import build, synth
+    build.build()
+    from paper_2510_18136_gb300 import native
+
+    cfg = synth.SearchConfig(ny=2, nx=3, n_t=40, dm=np.array([0.0, 0.0, 300.0, 900.0, 2500.0, 30000.0]),
+                             widths=np.array([1, 3, 8, 40], np.int32))
+    with native.Plan(cfg) as plan:
+        ops, n_u = bench.alg_ops(cfg, plan)
+    tab = oracle.delay_table(cfg.freq_mhz, cfg.dm, cfg.k_dm_ms, cfg.t_samp_ms)
+    rows = {tuple(int(s) for s in r) for r in tab}
+    assert max(max(r) for r in rows) >= cfg.n_t          # one row has no sample at all
+    want = 0
+    for r in rows:
+        L = cfg.n_t - max(r)
+        for _ in range(max(L, 0)):
+            want += (cfg.n_sub - 1) + 1
+        for w in cfg.widths:
+            for _ in range(max(L - int(w) + 1, 0)):
+                want += 2
+    assert n_u == len(rows) == len(cfg.dm) - 1
+    assert ops == want * cfg.n_pix
